@@ -1,0 +1,312 @@
+"""Pins for the FP64 CPU oracle.
+
+Each test checks the oracle against something other than itself: a closed form
+(the 2D DFT), a library routine (numpy's FFT and Chebyshev points), an
+invariant (polynomial reproduction, homogeneity, exactness for separable
+phases, the adjoint identity), brute force on tiny inputs, values the paper
+prints (Table 1) or the error behaviour the paper reports (Sec. 5)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_0809_0719_gb300.inputs import gaussian_sources, sample_indices
+
+ELL16 = [2.0, 1.0, 16.0, 1.0]     # ellipse phase of eq. ex1 with the constants scaled by 1/16
+ELL3 = [2.0, 1.0, 3.0, 1.0]       # eq. ex1 exactly (Table 1)
+CIRC20 = [3.0, 1.0, 20.0, 1.0]    # circle phase of eq. ex2 with c = (3 + sin sin)/20
+SEP = [0.3, 0.2, 0.25, 0.1]       # test-only separable phase
+
+
+def dft_of(f):
+    """u[i] = sum_k e^{2 pi i (i/N).k} f(k), k = m - N/2, written with numpy's inverse FFT."""
+    N = f.shape[0]
+    i = np.arange(N)
+    sign = (-1.0) ** (i[:, None] + i[None, :])
+    return sign * N * N * np.fft.ifft2(f)
+
+
+def expi(t):
+    return np.exp(2j * np.pi * (t - np.rint(t)))
+
+
+# ------------------------------------------------------------ direct sum
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_direct_linear_phase_is_a_2d_dft(oracle, N):
+    f = gaussian_sources(N, 11)
+    u = oracle.direct(N, oracle.LINEAR, [], f).reshape(N, N)
+    assert oracle.rel_l2(u, dft_of(f)) < 1e-12
+
+
+@pytest.mark.parametrize("N", [16, 32])
+def test_direct_circle_with_constant_speed_is_a_dft(oracle, N):
+    # Phi = x.k + c|k| with c constant: the DFT of f(k) e^{2 pi i c |k|}
+    c = 3.0 / 20.0
+    f = gaussian_sources(N, 12)
+    k = np.arange(N) - N // 2
+    kk = np.sqrt(k[:, None] ** 2 + k[None, :] ** 2)
+    u = oracle.direct(N, oracle.CIRCLE, [3.0, 0.0, 20.0, 1.0], f).reshape(N, N)
+    assert oracle.rel_l2(u, dft_of(f * np.exp(2j * np.pi * c * kk))) < 1e-12
+
+
+@pytest.mark.parametrize("N", [8, 32])
+def test_direct_adjoint_linear_phase_is_a_forward_dft(oracle, N):
+    g = gaussian_sources(N, 13)
+    i = np.arange(N)
+    sign = (-1.0) ** (i[:, None] + i[None, :])
+    ref = np.fft.fft2(sign * g)
+    fb = oracle.direct_adjoint(N, oracle.LINEAR, [], g).reshape(N, N)
+    assert oracle.rel_l2(fb, ref) < 1e-12
+
+
+def test_direct_sample_matches_full(oracle):
+    N = 32
+    f = gaussian_sources(N, 14)
+    xi = sample_indices(N, 77, 3)
+    full = oracle.direct(N, oracle.ELLIPSE, ELL16, f)
+    assert np.array_equal(oracle.direct(N, oracle.ELLIPSE, ELL16, f, xi), full[xi])
+
+
+# ------------------------------------------------- Chebyshev and Lagrange
+
+
+@pytest.mark.parametrize("q", [2, 3, 5, 9, 17])
+def test_chebyshev_grid_is_lobatto_grid(oracle, q):
+    ref = 0.5 * np.polynomial.chebyshev.chebpts2(q)[::-1]
+    assert np.allclose(oracle.cheb_nodes(q), ref, atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("q", [3, 5, 7, 9, 11])
+def test_lagrange_reproduces_polynomials(oracle, q):
+    rng = np.random.default_rng(q)
+    z = oracle.cheb_nodes(q)
+    coef = rng.standard_normal(q)
+    P = np.polynomial.polynomial.Polynomial(coef)
+    for t in np.concatenate([rng.uniform(-0.5, 0.5, 20), z]):
+        assert abs(np.dot(oracle.lagrange(q, t), P(z)) - P(t)) < 1e-12 * np.abs(coef).sum()
+    eye = np.array([oracle.lagrange(q, zz) for zz in z])
+    assert np.allclose(eye, np.eye(q), atol=1e-14)
+
+
+# ------------------------------------------------------ polar map, phases
+
+
+def test_polar_map_inverts_to_the_lattice(oracle):
+    N = 16
+    for k1 in range(-N // 2, N // 2):
+        for k2 in range(-N // 2, N // 2):
+            p1, p2 = oracle.polar(N, k1, k2)
+            assert 0.0 <= p1 <= 1.0 and 0.0 <= p2 < 1.0
+            r = np.sqrt(2) / 2 * N * p1
+            assert abs(r * np.cos(2 * np.pi * p2) - k1) < 1e-12 and abs(r * np.sin(2 * np.pi * p2) - k2) < 1e-12
+    assert oracle.polar(N, -N // 2, -N // 2)[0] == 1.0
+    assert oracle.polar(N, 0, 0) == (0.0, 0.0)
+
+
+@pytest.mark.parametrize("phase,prm", [(1, ELL16), (1, ELL3), (2, CIRC20), (0, [])])
+def test_phases_are_homogeneous_of_degree_one(oracle, phase, prm):
+    # Sec. 1: Phi(x, lambda k) = lambda Phi(x, k); and theta(x, p(k)) = Phi(x, k)
+    rng = np.random.default_rng(1)
+    N = 64
+    for _ in range(20):
+        x = rng.random(2)
+        k = rng.integers(-N // 2, N // 2, 2)
+        a = oracle.phi(phase, prm, N, x, k)
+        assert abs(oracle.phi(phase, prm, N, x, 3 * k) - 3 * a) < 1e-11 * (1 + abs(a))
+        assert abs(oracle.theta(phase, prm, N, x, oracle.polar(N, k[0], k[1])) - a) < 1e-11 * (1 + abs(a))
+
+
+# -------------------------------------------------------------- butterfly
+
+
+@pytest.mark.parametrize("N", [16, 64])
+@pytest.mark.parametrize("e", [0, 2])
+@pytest.mark.parametrize("s", [0, 3])
+@pytest.mark.parametrize("phase,prm", [(3, SEP), (2, [3.0, 0.0, 20.0, 0.0])])
+def test_butterfly_exact_when_residual_vanishes(oracle, N, e, s, phase, prm):
+    # eq. RAB: R^{AB} = 0 for a phase additively separable in (x, p), so every
+    # interpolation reproduces exactly (partition of unity) and the butterfly
+    # equals the direct sum up to rounding.  Wrong nodes, modulation signs or
+    # child indices break this.
+    f = gaussian_sources(N, 21)
+    ud = oracle.direct(N, phase, prm, f).reshape(N, N)
+    for q in (3, 5):
+        ub = oracle.butterfly(N, q, phase, prm, f, s=s, e=e)
+        assert oracle.rel_l2(ub, ud) < 1e-12
+
+
+def test_butterfly_error_falls_with_q(oracle):
+    # Sec. 5: the error is controlled by q, improving ~30x per q+2 on average
+    N = 64
+    f = gaussian_sources(N, 0)
+    ud = oracle.direct(N, oracle.ELLIPSE, ELL16, f).reshape(N, N)
+    err = [oracle.rel_l2(oracle.butterfly(N, q, oracle.ELLIPSE, ELL16, f, s=3, e=2), ud) for q in (5, 7, 9)]
+    for a, b in zip(err, err[1:]):
+        assert a / b > 10.0
+    assert err[2] < 3e-5
+
+
+def test_butterfly_error_nearly_flat_in_N(oracle):
+    # Sec. 5: the accuracy decreases only slightly as N grows
+    errs = []
+    for N in (64, 128):
+        f = gaussian_sources(N, 0)
+        xi = sample_indices(N, 256, 1000)
+        ud = oracle.direct(N, oracle.ELLIPSE, ELL16, f, xi)
+        ub = oracle.butterfly(N, 7, oracle.ELLIPSE, ELL16, f, s=3, e=2).ravel()[xi]
+        errs.append(oracle.rel_l2(ub, ud))
+    assert errs[1] < 3.0 * errs[0]
+
+
+def _table1():
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_ex1_eps.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            n, q, e = line.split()
+            rows[(int(n), int(q))] = float(e)
+    return rows
+
+
+@pytest.mark.parametrize("q", [5, 7, 9])
+def test_table1_accuracy_with_fine_angular_boxes(oracle, q):
+    # Table 1 (eq. ex1 with its /3 constants): with the angular side of the
+    # T_P boxes refined 16-fold (e=4) the oracle's eps_a lands within 3x of the
+    # printed N=64 values.
+    N = 64
+    f = gaussian_sources(N, 0)
+    xi = sample_indices(N, 256, 1000)
+    ud = oracle.direct(N, oracle.ELLIPSE, ELL3, f, xi)
+    eps = oracle.rel_l2(oracle.butterfly(N, q, oracle.ELLIPSE, ELL3, f, s=3, e=4).ravel()[xi], ud)
+    ref = _table1()[(N, q)]
+    assert ref / 3.0 < eps < ref * 3.0
+
+
+@pytest.mark.parametrize("e", [0, 2])
+def test_tiny_butterfly_matrix_and_its_adjoint(oracle, e):
+    # Brute force at N=8: build the butterfly's matrix column by column; its
+    # adjoint's matrix must be the exact conjugate transpose, and the matrix
+    # must approach the direct sum's as q grows.
+    N = 8
+    n = N * N
+    Kd = np.zeros((n, n), complex)
+    for j in range(n):
+        ej = np.zeros(n, complex)
+        ej[j] = 1.0
+        Kd[:, j] = oracle.direct(N, oracle.ELLIPSE, ELL16, ej)
+    errs = []
+    for q in (3, 4, 5):
+        B = np.zeros((n, n), complex)
+        Bh = np.zeros((n, n), complex)
+        for j in range(n):
+            ej = np.zeros(n, complex)
+            ej[j] = 1.0
+            B[:, j] = oracle.butterfly(N, q, oracle.ELLIPSE, ELL16, ej, s=0, e=e).ravel()
+            Bh[:, j] = oracle.butterfly_adjoint(N, q, oracle.ELLIPSE, ELL16, ej, s=0, e=e).ravel()
+        assert np.abs(Bh - B.conj().T).max() < 1e-13 * np.abs(B).max()
+        errs.append(np.linalg.norm(B - Kd) / np.linalg.norm(Kd))
+    assert errs[0] > errs[1] > errs[2]
+
+
+@pytest.mark.parametrize("N,s,e", [(32, 3, 2), (32, 0, 0), (64, 3, 2), (128, 3, 1)])
+def test_dot_test(oracle, N, s, e):
+    f = gaussian_sources(N, 31)
+    g = gaussian_sources(N, 32)
+    Bf = oracle.butterfly(N, 5, oracle.ELLIPSE, ELL16, f, s=s, e=e)
+    Bg = oracle.butterfly_adjoint(N, 5, oracle.ELLIPSE, ELL16, g, s=s, e=e)
+    a = np.vdot(g, Bf)
+    b = np.vdot(Bg, f)
+    assert abs(a - b) < 1e-13 * abs(a)
+
+
+def test_adjoint_butterfly_approximates_adjoint_sum(oracle):
+    N = 64
+    g = gaussian_sources(N, 41)
+    fb = oracle.butterfly_adjoint(N, 9, oracle.ELLIPSE, ELL16, g, s=3, e=2).ravel()
+    ki = sample_indices(N, 256, 1001)
+    ref = oracle.direct_adjoint(N, oracle.ELLIPSE, ELL16, g, ki)
+    assert oracle.rel_l2(fb[ki], ref) < 1e-4
+
+
+# ----------------------------------------------- per-level state identities
+
+
+def _box_members(oracle, N, j, e):
+    """dict (b1, b2) -> list of (k1, k2) with p(k) in that T_P box at level j."""
+    out = {}
+    for k1 in range(-N // 2, N // 2):
+        for k2 in range(-N // 2, N // 2):
+            p1, p2 = oracle.polar(N, k1, k2)
+            b1 = min(int(np.floor(p1 * (1 << j))), (1 << j) - 1)
+            b2 = min(int(np.floor(p2 * (1 << (j + e)))), (1 << (j + e)) - 1)
+            out.setdefault((b1, b2), []).append((k1, k2))
+    return out
+
+
+def _uB(oracle, N, phase, prm, f, members, x):
+    return sum(expi(oracle.phi(phase, prm, N, x, k)) * f[k[0] + N // 2, k[1] + N // 2] for k in members)
+
+
+def test_x_side_coefficients_are_potentials_at_x_nodes(oracle):
+    # eq. D2: after the switch, delta^{AB}_t ~ u^B(x^A_t)
+    N, q, s, e = 64, 9, 3, 2
+    L = 6
+    f = gaussian_sources(N, 51)
+    z = oracle.cheb_nodes(q)
+    stage = 1  # init, then the switch (lm = s = 3)
+    _, st = oracle.butterfly(N, q, oracle.ELLIPSE, ELL16, f, s=s, e=e, stage=stage)
+    lA = oracle.stage_level(N, s, -1, stage)
+    lB = L - lA
+    mem = _box_members(oracle, N, lB, e)
+    rng = np.random.default_rng(0)
+    worst = 0.0
+    scale = 0.0
+    for _ in range(6):
+        a = rng.integers(0, 1 << lA, 2)
+        b = max(mem, key=lambda bb: len(mem[bb]) + rng.random())
+        for t1, t2 in [(0, 0), (4, 5), (8, 2)]:
+            xt = ((a[0] + 0.5 + z[t1]) / (1 << lA), (a[1] + 0.5 + z[t2]) / (1 << lA))
+            ref = _uB(oracle, N, oracle.ELLIPSE, ELL16, f, mem[b], xt)
+            worst = max(worst, abs(st[a[0], a[1], b[0], b[1], t1, t2] - ref))
+            scale = max(scale, abs(ref))
+    assert worst < 1e-4 * scale
+
+
+def test_p_side_coefficients_are_equivalent_sources(oracle):
+    # Sec. 4, step 3: sum_t e^{2 pi i theta(x, p^B_t)} delta^{AB}_t ~ u^B(x) for x in A
+    N, q, s, e = 64, 9, 0, 2
+    L = 6
+    f = gaussian_sources(N, 52)
+    z = oracle.cheb_nodes(q)
+    stage = 2  # pairs with A at level 2, B at level 4
+    _, st = oracle.butterfly(N, q, oracle.ELLIPSE, ELL16, f, s=s, e=e, stage=stage)
+    lA = oracle.stage_level(N, s, -1, stage)
+    lB = L - lA
+    assert lA == 2
+    mem = _box_members(oracle, N, lB, e)
+    rng = np.random.default_rng(1)
+    worst = 0.0
+    scale = 0.0
+    for _ in range(8):
+        a = rng.integers(0, 1 << lA, 2)
+        b = max(mem, key=lambda bb: len(mem[bb]) + rng.random())
+        x = ((a[0] + rng.random()) / (1 << lA), (a[1] + rng.random()) / (1 << lA))
+        approx = 0
+        for t1 in range(q):
+            for t2 in range(q):
+                pt = ((b[0] + 0.5 + z[t1]) / (1 << lB), (b[1] + 0.5 + z[t2]) / (1 << (lB + e)))
+                approx += expi(oracle.theta(oracle.ELLIPSE, ELL16, N, x, pt)) * st[a[0], a[1], b[0], b[1], t1, t2]
+        ref = _uB(oracle, N, oracle.ELLIPSE, ELL16, f, mem[b], x)
+        worst = max(worst, abs(approx - ref))
+        scale = max(scale, abs(ref))
+    assert worst < 1e-4 * scale
+
+
+def test_oracle_rejects_bad_arguments(oracle):
+    f = np.zeros((48, 48), complex)
+    with pytest.raises(ValueError):
+        oracle.butterfly(48, 5, oracle.ELLIPSE, ELL16, f)
+    with pytest.raises(ValueError):
+        oracle.butterfly(64, 1, oracle.ELLIPSE, ELL16, np.zeros((64, 64), complex))
