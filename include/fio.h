@@ -1,0 +1,150 @@
+/*
+ * fio.h -- C ABI of the GB300 butterfly library for discrete Fourier integral
+ * operators (Candes, Demanet & Ying, "A Fast Butterfly Algorithm for the
+ * Computation of Fourier Integral Operators", 2008).
+ *
+ * The operator (Sec. 1, eq. dfio) is
+ *     u(x) = sum_{k in Omega} e^{2 pi i Phi(x,k)} f(k),   x in X,
+ * X = {(i1/N, i2/N): 0 <= i1,i2 < N}, Omega = {(k1,k2): -N/2 <= k1,k2 < N/2},
+ * N a power of two.  fio_apply evaluates it with the butterfly algorithm of
+ * Sec. 4 in the polar coordinates p of eq. polar (k = (sqrt2/2) N p1
+ * (cos 2 pi p2, sin 2 pi p2)), with the level truncation of Sec. 5:
+ *   initialization  (eq. alg2a)  pairs (A at level s, B at level L-s)
+ *   recursion in p  (eq. alg2b)  levels s+1 .. floor(L/2)
+ *   switch          (eq. alg2m)  at level floor(L/2)
+ *   recursion in x  (eq. alg2c)  levels floor(L/2)+1 .. L-s
+ *   termination     (eq. alg2d)  summing the boxes B at level s
+ * fio_apply_adjoint applies the exact conjugate transpose of that discrete
+ * butterfly (the steps above transposed and conjugated, in reverse order).
+ *
+ * Data layout (row-major, interleaved complex; complex128 for FIO_F64,
+ * complex64 for FIO_F32; a torch tensor of shape (nrhs, N, N)):
+ *   f, fbar : element (r, k1 + N/2, k2 + N/2) is the source of RHS r at (k1, k2)
+ *   u, g    : element (r, i1, i2) is the potential of RHS r at x = (i1/N, i2/N)
+ *
+ * Ownership: every data pointer passed in belongs to the caller and is never
+ * freed or retained past the call.  A plan owns its device tables and state
+ * buffers; fio_destroy releases them.  All work of fio_apply* is enqueued on
+ * the given CUDA stream (NULL = the legacy default stream) and the call returns
+ * without synchronising, except where stated.
+ *
+ * Errors: every entry point returns FIO_OK (0) or a negative status; nothing
+ * throws across the ABI.  fio_last_error() returns a thread-local message for
+ * the last failing call on the calling thread.  No entry point ever falls back
+ * to a CPU computation.
+ */
+#ifndef FIO_H_
+#define FIO_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fio_plan_s *fio_plan_t;
+
+enum {
+  FIO_OK = 0,
+  FIO_EINVAL = -1,   /* an argument is out of range or a pointer is NULL */
+  FIO_ENOMEM = -2,   /* a device or host allocation failed */
+  FIO_ECUDA = -3,    /* a CUDA runtime call failed (message has the CUDA error) */
+  FIO_ETIMEOUT = -4, /* reserved: a bounded device-side wait expired */
+  FIO_EDEVICE = -5   /* no usable CUDA device */
+};
+
+/* Arithmetic forms.  FIO_F64: every step in FP64.  FIO_F32: coefficients,
+ * interpolation and accumulation in FP32; every phase Phi(x,k) is evaluated and
+ * reduced modulo 1 in FP64 before an FP32 sin/cos; node tables in FP64. */
+enum { FIO_F64 = 0, FIO_F32 = 1 };
+
+/* Phase functions Phi(x,k), params = [a, m, b, lambda] where used:
+ *   LINEAR          Phi = x.k                                   (no params)
+ *   ELLIPSE         Phi = lambda x.k + sqrt(c1^2 k1^2 + c2^2 k2^2),
+ *                   c1 = (a + m sin 2pi x1 sin 2pi x2)/b, c2 = (a + m cos 2pi x1 cos 2pi x2)/b
+ *                   (eq. ex1 is [2, 1, 3, 1])
+ *   CIRCLE          Phi = lambda x.k + c |k|, c = (a + m sin 2pi x1 sin 2pi x2)/b
+ *                   (the phase of eq. ex2 is [3, 1, 4, 1])
+ *   TEST_SEPARABLE  N Psi(x,p) = N (a sin 2pi x1 cos 2pi x2 + m x1 x2 + b p1 cos 2pi p2 + lambda p1^2);
+ *                   its residual R^{AB} (eq. RAB) vanishes, so the butterfly is exact (tests only). */
+enum { FIO_PHASE_LINEAR = 0, FIO_PHASE_ELLIPSE = 1, FIO_PHASE_CIRCLE = 2, FIO_PHASE_TEST_SEPARABLE = 3 };
+
+/*
+ * fio_plan -- build a plan for N x N grids (host work in FP64, then one upload).
+ *   N         power of two, 4 <= N <= 4096
+ *   q         Chebyshev points per dimension (Sec. 3.2); one of 3, 5, 7, 9, 11
+ *   phase_id  FIO_PHASE_*; params/nparams: 0 (LINEAR) or 4 doubles (others)
+ *   precision FIO_F64 or FIO_F32
+ *   nrhs_max  largest nrhs later passed to fio_apply* (>= 1); sizes the state
+ *   s         truncation depth of Sec. 5 (-1 = 3); clipped to floor(L/2)
+ *   e         angular refinement of the T_P boxes: a box at level j has width
+ *             2^-j in p1 and 2^-(j+e) in p2 (-1 = 2; 0 is the square-box
+ *             statement of Sec. 1.1; 0 <= e <= 4)
+ * Allocates device memory on the current CUDA device; the plan may only be
+ * used with that device current.  Returns FIO_EINVAL for bad arguments,
+ * FIO_ENOMEM when the state does not fit, FIO_EDEVICE without a device.
+ */
+int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, int nparams, int precision,
+             int nrhs_max, int s, int e);
+
+/* fio_destroy -- free a plan (waits for the device to finish with it). NULL is a no-op. */
+int fio_destroy(fio_plan_t plan);
+
+/*
+ * fio_apply -- u = B f for nrhs right-hand sides (Sec. 4, eqs. alg2a-alg2d).
+ *   f, u   DEVICE pointers, layout above, complex dtype of the plan's precision;
+ *          must not overlap; 16-byte aligned
+ *   nrhs   1 <= nrhs <= nrhs_max
+ *   stream cudaStream_t (as void*), NULL = default stream
+ */
+int fio_apply(fio_plan_t plan, const void *f, void *u, int nrhs, void *stream);
+
+/* fio_apply_adjoint -- fbar = B^H g, the exact conjugate transpose of fio_apply.
+ * g has u's layout, fbar has f's; DEVICE pointers; otherwise as fio_apply. */
+int fio_apply_adjoint(fio_plan_t plan, const void *g, void *fbar, int nrhs, void *stream);
+
+/*
+ * fio_apply_host -- fio_apply (adjoint != 0: fio_apply_adjoint) on HOST buffers.
+ * Copies the input to a plan-owned device staging buffer, applies, copies the
+ * output back and synchronises the stream before returning.  Host buffers
+ * should be page-locked for asynchronous copies.
+ */
+int fio_apply_host(fio_plan_t plan, const void *in_host, void *out_host, int nrhs, int adjoint, void *stream);
+
+/*
+ * fio_debug_stage -- run the forward butterfly on f (DEVICE, one RHS taken as
+ * RHS 0 of an nrhs=1 call) up to stage j and copy that state into out (DEVICE,
+ * complex128).  Stages: 0 initialization, then one per p-level, the switch, one
+ * per x-level (fio_plan_info().nstages in all).  out holds the pairs (A,B) at
+ * the stage's level l as [a1][a2][b1][b2][t1][t2], a in [0,2^l)^2,
+ * b in [0,2^(L-l)) x [0,2^(L-l+e)), t in [0,q)^2.  Synchronises the stream.
+ */
+int fio_debug_stage(fio_plan_t plan, const void *f, int stage, void *out, void *stream);
+
+typedef struct {
+  int N, L, q, s, e, l0, lm, l1, phase_id, precision, nrhs_max;
+  int nstages;             /* init + (lm-l0) p-levels + switch + (l1-lm) x-levels */
+  long long pairs_per_level; /* 2^e N^2 */
+  long long state_bytes;   /* device bytes of the two state buffers */
+  long long table_bytes;   /* device bytes of the plan's tables */
+  int max_box_sources;     /* most sources in one initialization box B */
+} fio_plan_info_t;
+
+/* fio_plan_info -- copy the plan's parameters and sizes into *info. */
+int fio_plan_info(fio_plan_t plan, fio_plan_info_t *info);
+
+/* fio_kernel_launches -- number of kernels one fio_apply (adjoint != 0: fio_apply_adjoint)
+ * with nrhs right-hand sides enqueues. */
+int fio_kernel_launches(fio_plan_t plan, int nrhs, int adjoint);
+
+/* fio_last_error -- thread-local message of the last failing call ("" if none). */
+const char *fio_last_error(void);
+
+/* fio_version -- library version number. */
+int fio_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIO_H_ */

@@ -1,0 +1,442 @@
+// fio_plan.cu -- plan construction (host, FP64) and the C ABI of include/fio.h.
+//
+// A plan holds, on the device, every table the kernels read:
+//   * node coordinates of the boxes of T_X and T_P at every level (Sec. 3.2
+//     Chebyshev grid adapted to a box: centre + width * z_j), with sin/cos of
+//     the x coordinates and the polar factors (sqrt2/2) N p1, cos/sin 2 pi p2 of
+//     the p coordinates (Sec. 1.1, eq. polar);
+//   * the sources k of Omega sorted by their box B at level L - s, with the two
+//     1D Lagrange weight vectors L_j(phat) of each (eq. alg2a);
+//   * two state buffers (only two consecutive levels are ever live, Sec. 4).
+// The 1D translation matrices T^0, T^1 and the termination matrix V are
+// position- and level-independent (Sec. 4) and travel as kernel arguments.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fio.h"
+#include "fio_run.cuh"
+
+namespace fio {
+int run_q3(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
+int run_q5(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
+int run_q7(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
+int run_q9(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
+int run_q11(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
+}  // namespace fio
+
+struct fio_plan_s {
+  fio::PlanDev d;
+  int device;
+  void *tables;
+  long long table_bytes, state_bytes;
+  void *stage_buf[2];
+  size_t stage_bytes;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? FIO_ENOMEM : FIO_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+const double kTwoPi = 6.283185307179586476925286766559;
+
+// Chebyshev grid of order q on [-1/2, 1/2], z_j = cos(j pi/(q-1))/2, written in
+// the sine form sin(pi (q-1-2j) / (2(q-1)))/2, which is exactly antisymmetric.
+void cheb_grid(int q, double *z) {
+  for (int j = 0; j < q; j++) z[j] = 0.5 * std::sin(M_PI * (q - 1 - 2 * j) / (2.0 * (q - 1)));
+}
+
+// All q Lagrange polynomials of the grid at t, barycentric form (second kind)
+// with the Chebyshev-Lobatto weights (-1)^j, halved at both ends.
+void lagrange_all(int q, const double *z, double t, double *out) {
+  double den = 0.0;
+  for (int j = 0; j < q; j++) {
+    if (t == z[j]) {
+      for (int i = 0; i < q; i++) out[i] = i == j ? 1.0 : 0.0;
+      return;
+    }
+  }
+  for (int j = 0; j < q; j++) {
+    double w = (j & 1) ? -1.0 : 1.0;
+    if (j == 0 || j == q - 1) w *= 0.5;
+    out[j] = w / (t - z[j]);
+    den += out[j];
+  }
+  for (int j = 0; j < q; j++) out[j] /= den;
+}
+
+bool q_supported(int q) { return q == 3 || q == 5 || q == 7 || q == 9 || q == 11; }
+
+int dispatch(const fio::PlanDev &d, int kind, const void *in, void *out, int nrhs, cudaStream_t st, int stop,
+             int *launches) {
+  switch (d.q) {
+  case 3: return fio::run_q3(d, kind, in, out, nrhs, st, stop, launches);
+  case 5: return fio::run_q5(d, kind, in, out, nrhs, st, stop, launches);
+  case 7: return fio::run_q7(d, kind, in, out, nrhs, st, stop, launches);
+  case 9: return fio::run_q9(d, kind, in, out, nrhs, st, stop, launches);
+  case 11: return fio::run_q11(d, kind, in, out, nrhs, st, stop, launches);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int check_device(fio_plan_t p) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != p->device) return fail(FIO_EINVAL, "plan was built on device %d but device %d is current", p->device, dev);
+  return FIO_OK;
+}
+
+size_t elem_bytes(const fio_plan_t p) { return p->d.precision == FIO_F64 ? 16 : 8; }
+
+}  // namespace
+
+extern "C" {
+
+const char *fio_last_error(void) { return g_err.c_str(); }
+
+int fio_version(void) { return 1; }
+
+int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, int nparams, int precision,
+             int nrhs_max, int s, int e) {
+  using namespace fio;
+  if (!out) return fail(FIO_EINVAL, "out is NULL");
+  *out = nullptr;
+  int L = 0;
+  while ((1 << L) < N && L < 30) L++;
+  if (N < 4 || N > 4096 || (1 << L) != N) return fail(FIO_EINVAL, "N=%d must be a power of two in [4, 4096]", N);
+  if (!q_supported(q)) return fail(FIO_EINVAL, "q=%d not supported (compiled for 3, 5, 7, 9, 11)", q);
+  if (phase_id < 0 || phase_id > 3) return fail(FIO_EINVAL, "unknown phase_id %d", phase_id);
+  if (phase_id != FIO_PHASE_LINEAR && (nparams != 4 || !params))
+    return fail(FIO_EINVAL, "phase %d needs 4 params, got %d", phase_id, nparams);
+  if (phase_id == FIO_PHASE_LINEAR && nparams != 0 && nparams != 4)
+    return fail(FIO_EINVAL, "linear phase takes no params, got %d", nparams);
+  if (precision != FIO_F64 && precision != FIO_F32) return fail(FIO_EINVAL, "unknown precision %d", precision);
+  if (nrhs_max < 1) return fail(FIO_EINVAL, "nrhs_max=%d must be >= 1", nrhs_max);
+  if (s < 0) s = 3;
+  if (s > L / 2) s = L / 2;
+  if ((1 << s) > kMMax) return fail(FIO_EINVAL, "s=%d too large", s);
+  if (e < 0) e = 2;
+  if (e > 4) return fail(FIO_EINVAL, "e=%d must be in [0, 4]", e);
+  if (phase_id == FIO_PHASE_ELLIPSE || phase_id == FIO_PHASE_CIRCLE) {
+    if (params[2] == 0.0) return fail(FIO_EINVAL, "params[2] (b) must be nonzero");
+  }
+
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(FIO_EDEVICE, "no CUDA device: %s", cudaGetErrorString(ce));
+
+  fio_plan_s *p = new (std::nothrow) fio_plan_s();
+  if (!p) return fail(FIO_ENOMEM, "host allocation failed");
+  p->device = dev;
+  PlanDev &d = p->d;
+  d.N = N;
+  d.L = L;
+  d.q = q;
+  d.s = s;
+  d.e = e;
+  d.l0 = s;
+  d.lm = L / 2;
+  d.l1 = L - s;
+  d.precision = precision;
+  d.nrhs_max = nrhs_max;
+  cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+
+  d.ph = Phase();
+  d.ph.id = phase_id;
+  d.ph.N = N;
+  if (phase_id == FIO_PHASE_ELLIPSE || phase_id == FIO_PHASE_CIRCLE) {
+    d.ph.a = params[0];
+    d.ph.m = params[1];
+    d.ph.ib = 1.0 / params[2];
+    d.ph.lam = params[3];
+  } else if (phase_id == FIO_PHASE_TEST_SEPARABLE) {
+    d.ph.sa = params[0];
+    d.ph.sm = params[1];
+    d.ph.sb = params[2];
+    d.ph.sl = params[3];
+  }
+
+  // ---- host tables
+  double z[kQMax];
+  cheb_grid(q, z);
+  double lg[kQMax];
+  memset(d.T, 0, sizeof d.T);
+  for (int sg = 0; sg < 2; sg++)
+    for (int jp = 0; jp < q; jp++) {
+      lagrange_all(q, z, (2 * sg - 1) / 4.0 + 0.5 * z[jp], lg);
+      for (int j = 0; j < q; j++) d.T[sg][j][jp] = lg[j];
+    }
+  memset(d.V, 0, sizeof d.V);
+  const int M = 1 << s;
+  for (int m = 0; m < M; m++) {
+    lagrange_all(q, z, (double)m / M - 0.5, lg);
+    for (int j = 0; j < q; j++) d.V[m][j] = lg[j];
+  }
+
+  std::vector<XNode> xnode;
+  std::vector<P1Node> p1node;
+  std::vector<P2Node> p2node;
+  for (int l = 0; l <= L; l++) {
+    d.tb.xoff[l] = (int)xnode.size();
+    d.tb.p1off[l] = (int)p1node.size();
+    d.tb.p2off[l] = (int)p2node.size();
+    const double w = 1.0 / (double)(1 << l);
+    for (int a = 0; a < (1 << l); a++)
+      for (int j = 0; j <= q; j++) {
+        XNode n;
+        n.x = (a + 0.5 + (j < q ? z[j] : 0.0)) * w;
+        n.s = std::sin(kTwoPi * n.x);
+        n.c = std::cos(kTwoPi * n.x);
+        xnode.push_back(n);
+        P1Node u;
+        u.p1 = n.x;
+        u.rho = 0.5 * std::sqrt(2.0) * N * u.p1;
+        p1node.push_back(u);
+      }
+    const double w2 = 1.0 / (double)(1LL << (l + e));
+    for (long long b = 0; b < (1LL << (l + e)); b++)
+      for (int j = 0; j <= q; j++) {
+        const double p2 = (b + 0.5 + (j < q ? z[j] : 0.0)) * w2;
+        P2Node v;
+        v.c = std::cos(kTwoPi * p2);
+        v.s = std::sin(kTwoPi * p2);
+        p2node.push_back(v);
+      }
+  }
+  std::vector<XNode> xgrid(N);
+  for (int i = 0; i < N; i++) {
+    xgrid[i].x = (double)i / N;
+    xgrid[i].s = std::sin(kTwoPi * xgrid[i].x);
+    xgrid[i].c = std::cos(kTwoPi * xgrid[i].x);
+  }
+
+  // sources sorted by their box B at level lb = L - s (eq. alg2a)
+  const int lb = L - d.l0;
+  const long long nb1 = 1LL << lb, nb2 = 1LL << (lb + e);
+  const long long nbox = nb1 * nb2;
+  const long long NN = (long long)N * N;
+  std::vector<long long> boxof(NN);
+  std::vector<double> P1(NN), P2(NN);
+  std::vector<int> cnt(nbox + 1, 0);
+  for (long long kf = 0; kf < NN; kf++) {
+    const int k1 = (int)(kf / N) - N / 2, k2 = (int)(kf % N) - N / 2;
+    const double kk = (double)k1 * k1 + (double)k2 * k2;
+    const double p1 = std::sqrt(2.0 * kk) / N;
+    double ang = std::atan2((double)k2, (double)k1) / kTwoPi;
+    if (ang < 0.0) ang += 1.0;
+    if (k1 == 0 && k2 == 0) ang = 0.0;
+    long long b1 = (long long)std::floor(p1 * (double)nb1);
+    long long b2 = (long long)std::floor(ang * (double)nb2);
+    if (b1 > nb1 - 1) b1 = nb1 - 1;
+    if (b2 > nb2 - 1) b2 = nb2 - 1;
+    boxof[kf] = b1 * nb2 + b2;
+    P1[kf] = p1;
+    P2[kf] = ang;
+    cnt[boxof[kf] + 1]++;
+  }
+  int maxsrc = 0;
+  for (long long b = 0; b < nbox; b++) {
+    maxsrc = std::max(maxsrc, cnt[b + 1]);
+    cnt[b + 1] += cnt[b];
+  }
+  std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+  std::vector<Src> src(NN);
+  std::vector<int> srcf(NN);
+  std::vector<double> srcw(NN * 2 * q);
+  for (long long kf = 0; kf < NN; kf++) {
+    const int j = pos[boxof[kf]]++;
+    const int k1 = (int)(kf / N) - N / 2, k2 = (int)(kf % N) - N / 2;
+    Src sc;
+    sc.k1 = k1;
+    sc.k2 = k2;
+    sc.kr = std::sqrt((double)k1 * k1 + (double)k2 * k2);
+    sc.p1 = P1[kf];
+    sc.c2 = std::cos(kTwoPi * P2[kf]);
+    src[j] = sc;
+    srcf[j] = (int)kf;
+    const long long b1 = boxof[kf] / nb2, b2 = boxof[kf] % nb2;
+    const double h1 = P1[kf] * (double)nb1 - (double)b1 - 0.5;
+    const double h2 = P2[kf] * (double)nb2 - (double)b2 - 0.5;
+    lagrange_all(q, z, h1, &srcw[(size_t)j * 2 * q]);
+    lagrange_all(q, z, h2, &srcw[(size_t)j * 2 * q + q]);
+  }
+  d.maxsrc = maxsrc;
+  d.nbox_init = (int)nbox;
+
+  // ---- device: one table allocation, two state buffers
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t b_x = al(xnode.size() * sizeof(XNode)), b_p1 = al(p1node.size() * sizeof(P1Node)),
+               b_p2 = al(p2node.size() * sizeof(P2Node)), b_g = al(N * sizeof(XNode)), b_s = al(NN * sizeof(Src)),
+               b_f = al(NN * sizeof(int)), b_w = al(srcw.size() * sizeof(double)), b_o = al((nbox + 1) * sizeof(int));
+  const size_t tbytes = b_x + b_p1 + b_p2 + b_g + b_s + b_f + b_w + b_o;
+  const size_t sbytes = (((size_t)NN * q * q) << e) * (size_t)nrhs_max * (precision == FIO_F64 ? 16 : 8);
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  if (tbytes + 2 * sbytes > freeb) {
+    delete p;
+    return fail(FIO_ENOMEM, "plan needs %.2f GB of device memory, %.2f GB free", (tbytes + 2.0 * sbytes) / 1e9,
+                freeb / 1e9);
+  }
+  char *tb = nullptr;
+  if ((ce = cudaMalloc((void **)&tb, tbytes)) != cudaSuccess) {
+    delete p;
+    return cuda_fail(ce, "cudaMalloc(tables)");
+  }
+  p->tables = tb;
+  p->table_bytes = (long long)tbytes;
+  size_t off = 0;
+  auto up = [&](const void *h, size_t n, size_t blk) {
+    void *dptr = tb + off;
+    if (n) cudaMemcpy(dptr, h, n, cudaMemcpyHostToDevice);
+    off += blk;
+    return dptr;
+  };
+  d.tb.xnode = (const XNode *)up(xnode.data(), xnode.size() * sizeof(XNode), b_x);
+  d.tb.p1node = (const P1Node *)up(p1node.data(), p1node.size() * sizeof(P1Node), b_p1);
+  d.tb.p2node = (const P2Node *)up(p2node.data(), p2node.size() * sizeof(P2Node), b_p2);
+  d.tb.xgrid = (const XNode *)up(xgrid.data(), N * sizeof(XNode), b_g);
+  d.tb.src = (const Src *)up(src.data(), NN * sizeof(Src), b_s);
+  d.tb.src_f = (const int *)up(srcf.data(), NN * sizeof(int), b_f);
+  d.tb.src_w = (const double *)up(srcw.data(), srcw.size() * sizeof(double), b_w);
+  d.tb.box_off = (const int *)up(cnt.data(), (nbox + 1) * sizeof(int), b_o);
+  if ((ce = cudaGetLastError()) != cudaSuccess) {
+    cudaFree(tb);
+    delete p;
+    return cuda_fail(ce, "table upload");
+  }
+  for (int i = 0; i < 2; i++) {
+    if ((ce = cudaMalloc(&d.state[i], sbytes)) != cudaSuccess) {
+      if (i) cudaFree(d.state[0]);
+      cudaFree(tb);
+      delete p;
+      return cuda_fail(ce, "cudaMalloc(state)");
+    }
+  }
+  p->state_bytes = 2LL * (long long)sbytes;
+  *out = p;
+  g_err.clear();
+  return FIO_OK;
+}
+
+int fio_destroy(fio_plan_t p) {
+  if (!p) return FIO_OK;
+  cudaDeviceSynchronize();
+  cudaFree(p->d.state[0]);
+  cudaFree(p->d.state[1]);
+  cudaFree(p->tables);
+  cudaFree(p->stage_buf[0]);
+  cudaFree(p->stage_buf[1]);
+  delete p;
+  return FIO_OK;
+}
+
+static int apply_common(fio_plan_t p, int kind, const void *in, void *out, int nrhs, void *stream) {
+  if (!p) return fail(FIO_EINVAL, "plan is NULL");
+  if (!in || !out) return fail(FIO_EINVAL, "NULL data pointer");
+  if (nrhs < 1 || nrhs > p->d.nrhs_max) return fail(FIO_EINVAL, "nrhs=%d outside [1, %d]", nrhs, p->d.nrhs_max);
+  if (((uintptr_t)in | (uintptr_t)out) & 15) return fail(FIO_EINVAL, "data pointers must be 16-byte aligned");
+  int rc = check_device(p);
+  if (rc) return rc;
+  rc = dispatch(p->d, kind, in, out, nrhs, (cudaStream_t)stream, -1, nullptr);
+  if (rc) return cuda_fail((cudaError_t)rc, kind == fio::RUN_FWD ? "fio_apply" : "fio_apply_adjoint");
+  return FIO_OK;
+}
+
+int fio_apply(fio_plan_t p, const void *f, void *u, int nrhs, void *stream) {
+  return apply_common(p, fio::RUN_FWD, f, u, nrhs, stream);
+}
+
+int fio_apply_adjoint(fio_plan_t p, const void *g, void *fbar, int nrhs, void *stream) {
+  return apply_common(p, fio::RUN_ADJ, g, fbar, nrhs, stream);
+}
+
+int fio_apply_host(fio_plan_t p, const void *in_host, void *out_host, int nrhs, int adjoint, void *stream) {
+  if (!p) return fail(FIO_EINVAL, "plan is NULL");
+  if (!in_host || !out_host) return fail(FIO_EINVAL, "NULL host pointer");
+  if (nrhs < 1 || nrhs > p->d.nrhs_max) return fail(FIO_EINVAL, "nrhs=%d outside [1, %d]", nrhs, p->d.nrhs_max);
+  int rc = check_device(p);
+  if (rc) return rc;
+  const size_t per = (size_t)p->d.N * p->d.N * elem_bytes(p);
+  if (!p->stage_buf[0]) {
+    const size_t bytes = per * p->d.nrhs_max;
+    cudaError_t ce;
+    for (int i = 0; i < 2; i++)
+      if ((ce = cudaMalloc(&p->stage_buf[i], bytes)) != cudaSuccess) return cuda_fail(ce, "cudaMalloc(staging)");
+    p->stage_bytes = bytes;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = per * nrhs;
+  cudaError_t ce = cudaMemcpyAsync(p->stage_buf[0], in_host, n, cudaMemcpyHostToDevice, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemcpyAsync H2D");
+  rc = apply_common(p, adjoint ? fio::RUN_ADJ : fio::RUN_FWD, p->stage_buf[0], p->stage_buf[1], nrhs, stream);
+  if (rc) return rc;
+  if ((ce = cudaMemcpyAsync(out_host, p->stage_buf[1], n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(ce, "cudaMemcpyAsync D2H");
+  if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+  return FIO_OK;
+}
+
+int fio_debug_stage(fio_plan_t p, const void *f, int stage, void *out, void *stream) {
+  if (!p || !f || !out) return fail(FIO_EINVAL, "NULL argument");
+  const int nst = (p->d.lm - p->d.l0) + 2 + (p->d.l1 - p->d.lm);
+  if (stage < 0 || stage >= nst) return fail(FIO_EINVAL, "stage %d outside [0, %d)", stage, nst);
+  int rc = check_device(p);
+  if (rc) return rc;
+  rc = dispatch(p->d, fio::RUN_FWD, f, out, 1, (cudaStream_t)stream, stage, nullptr);
+  if (rc) return cuda_fail((cudaError_t)rc, "fio_debug_stage");
+  cudaError_t ce = cudaStreamSynchronize((cudaStream_t)stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+  return FIO_OK;
+}
+
+int fio_plan_info(fio_plan_t p, fio_plan_info_t *info) {
+  if (!p || !info) return fail(FIO_EINVAL, "NULL argument");
+  const fio::PlanDev &d = p->d;
+  info->N = d.N;
+  info->L = d.L;
+  info->q = d.q;
+  info->s = d.s;
+  info->e = d.e;
+  info->l0 = d.l0;
+  info->lm = d.lm;
+  info->l1 = d.l1;
+  info->phase_id = d.ph.id;
+  info->precision = d.precision;
+  info->nrhs_max = d.nrhs_max;
+  info->nstages = (d.lm - d.l0) + 2 + (d.l1 - d.lm);
+  info->pairs_per_level = ((long long)d.N * d.N) << d.e;
+  info->state_bytes = p->state_bytes;
+  info->table_bytes = p->table_bytes;
+  info->max_box_sources = d.maxsrc;
+  return FIO_OK;
+}
+
+int fio_kernel_launches(fio_plan_t p, int nrhs, int adjoint) {
+  if (!p) return fail(FIO_EINVAL, "plan is NULL");
+  int n = 0;
+  dispatch(p->d, adjoint ? fio::RUN_COUNT_ADJ : fio::RUN_COUNT_FWD, nullptr, nullptr, nrhs, nullptr, -1, &n);
+  return n;
+}
+
+}  // extern "C"

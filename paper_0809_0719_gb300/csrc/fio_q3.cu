@@ -1,0 +1,9 @@
+// fio_q3.cu -- the butterfly kernels instantiated for q = 3 (both precisions).
+#include "fio_run.cuh"
+
+namespace fio {
+int run_q3(const PlanDev &p, int kind, const void *in, void *out, int nrhs, cudaStream_t st, int stop, int *launches) {
+  return p.precision == 0 ? run_plan<double, 3>(p, kind, in, out, nrhs, st, stop, launches)
+                          : run_plan<float, 3>(p, kind, in, out, nrhs, st, stop, launches);
+}
+}  // namespace fio

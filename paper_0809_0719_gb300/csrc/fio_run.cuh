@@ -1,0 +1,251 @@
+// fio_run.cuh -- launch shapes and the level schedule of one apply (forward or
+// adjoint), templated on precision R and q.  Included once per q by fio_q*.cu.
+#pragma once
+#include <algorithm>
+
+#include "fio_kernels.cuh"
+
+namespace fio {
+
+// Everything a run needs from a plan (plain data, no ownership).
+struct PlanDev {
+  Tables tb;
+  Phase ph;
+  int N, L, q, s, e, l0, lm, l1, precision, nrhs_max, maxsrc, nbox_init;
+  void *state[2];
+  double T[2][kQMax][kQMax];
+  double V[kMMax][kQMax];
+  int smem_optin;
+};
+
+enum RunKind { RUN_FWD = 0, RUN_ADJ = 1, RUN_COUNT_FWD = 2, RUN_COUNT_ADJ = 3 };
+
+constexpr int kSmemTarget = 100 * 1024;  // per-CTA budget of the translation kernels
+
+template <typename K> static cudaError_t set_smem(K kernel, int optin) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+template <typename R, int Q> struct Runner {
+  typedef typename C2<R>::T CT;
+  static constexpr int Q2 = Q * Q;
+  const PlanDev &p;
+  cudaStream_t st;
+  int nrhs;
+  bool count_only;
+  int launches = 0;
+
+  Runner(const PlanDev &pp, cudaStream_t s, int n, bool c) : p(pp), st(s), nrhs(n), count_only(c) {}
+
+  Geom geom(int l, int rt, int U, long long nunits) const {
+    Geom g;
+    g.L = p.L;
+    g.e = p.e;
+    g.q = Q;
+    g.s = p.s;
+    g.l = l;
+    g.nrhs = nrhs;
+    g.rt = rt;
+    g.U = U;
+    g.nunits = nunits;
+    return g;
+  }
+  TMat<R, Q> tmat() const {
+    TMat<R, Q> t;
+    for (int s = 0; s < 2; s++)
+      for (int i = 0; i < Q; i++)
+        for (int j = 0; j < Q; j++) t.T[s][i][j] = (R)p.T[s][i][j];
+    return t;
+  }
+  VMat<R, Q> vmat() const {
+    VMat<R, Q> v;
+    for (int m = 0; m < kMMax; m++)
+      for (int j = 0; j < Q; j++) v.V[m][j] = (R)p.V[m][j];
+    return v;
+  }
+  long long nb_at(int lb) const { return (1LL << lb) << (lb + p.e); }
+
+  int check() {
+    launches++;
+    if (count_only) return 0;
+    cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? 0 : (int)err;
+  }
+
+  // Translation at level l (forward: l-1 -> l; adjoint: l -> l-1).
+  template <bool TYPE_P, bool FWD> int trans(int l, const CT *in, CT *out) {
+    const int rt = std::min(nrhs, sizeof(R) == 4 ? 8 : 4);
+    const int per_unit = (12 * rt * Q2 + 20 * Q2) * (int)sizeof(CT);
+    int U = std::max(1, (64 + rt * Q - 1) / (rt * Q));
+    U = std::max(1, std::min(U, kSmemTarget / per_unit));
+    const long long nunits = (1LL << (2 * (l - 1))) * nb_at(p.L - l);
+    const Geom g = geom(l, rt, U, nunits);
+    dim3 grid((unsigned)((nunits + U - 1) / U), (unsigned)((nrhs + rt - 1) / rt));
+    const int smem = U * per_unit;
+    if (count_only) return check();
+    if (TYPE_P) {
+      auto k = k_trans_p<R, Q, FWD>;
+      set_smem(k, p.smem_optin);
+      k<<<grid, kThreads, smem, st>>>(p.tb, p.ph, g, tmat(), in, out);
+    } else {
+      auto k = k_trans_x<R, Q, FWD>;
+      set_smem(k, p.smem_optin);
+      k<<<grid, kThreads, smem, st>>>(p.tb, p.ph, g, tmat(), in, out);
+    }
+    return check();
+  }
+
+  template <bool FWD> int sw(const CT *in, CT *out) {
+    const int rt = std::min(nrhs, 32);
+    const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
+    int U = 1;
+    if (rt * Q2 < 1024) U = std::max(1, std::min(8, 1024 / (rt * Q2)));
+    const int kbudget = 64 * 1024;
+    int TC = std::max(1, std::min(Q2, kbudget / (U * Q2 * (int)sizeof(CT))));
+    const int smem = (U * rt * Q2 + U * TC * Q2) * (int)sizeof(CT);
+    const Geom g = geom(p.lm, rt, U, pairs);
+    dim3 grid((unsigned)((pairs + U - 1) / U), (unsigned)((nrhs + rt - 1) / rt));
+    if (count_only) return check();
+    auto k = k_switch<R, Q, FWD>;
+    set_smem(k, p.smem_optin);
+    k<<<grid, kThreads, smem, st>>>(p.tb, p.ph, g, TC, in, out);
+    return check();
+  }
+
+  int init(const CT *f, CT *out) {
+    const int ms = std::max(1, p.maxsrc);
+    int rt = std::min(nrhs, sizeof(R) == 4 ? 32 : 8);
+    int GA = std::max(1, kThreads / (rt * Q));
+    auto bytes = [&](int rt_, int ga) {
+      return (ms * rt_ + ga * ms + ga * Q2) * (int)sizeof(CT) + ms * 2 * Q * (int)sizeof(R);
+    };
+    while (bytes(rt, GA) > p.smem_optin && GA > 1) GA--;
+    while (bytes(rt, GA) > p.smem_optin && rt > 1) rt--;
+    if (bytes(rt, GA) > p.smem_optin) return (int)cudaErrorInvalidConfiguration;
+    const Geom g = geom(p.l0, rt, 1, p.nbox_init);
+    dim3 grid((unsigned)p.nbox_init, (unsigned)((nrhs + rt - 1) / rt));
+    if (count_only) return check();
+    auto k = k_init<R, Q>;
+    set_smem(k, p.smem_optin);
+    k<<<grid, kThreads, bytes(rt, GA), st>>>(p.tb, p.ph, g, ms, GA, f, out);
+    return check();
+  }
+
+  int init_adj(const CT *in, CT *fbar) {
+    const int ms = std::max(1, p.maxsrc);
+    int rt = std::min(nrhs, sizeof(R) == 4 ? 32 : 8);
+    auto bytes = [&](int rt_) {
+      return (ms * rt_ + ms + Q2 + rt_ * Q2) * (int)sizeof(CT) + ms * 2 * Q * (int)sizeof(R);
+    };
+    while (bytes(rt) > p.smem_optin && rt > 1) rt--;
+    if (bytes(rt) > p.smem_optin) return (int)cudaErrorInvalidConfiguration;
+    const Geom g = geom(p.l0, rt, 1, p.nbox_init);
+    dim3 grid((unsigned)p.nbox_init, (unsigned)((nrhs + rt - 1) / rt));
+    if (count_only) return check();
+    auto k = k_init_adj<R, Q>;
+    set_smem(k, p.smem_optin);
+    k<<<grid, kThreads, bytes(rt), st>>>(p.tb, p.ph, g, ms, in, fbar);
+    return check();
+  }
+
+  int term(const CT *in, CT *u) {
+    const int M = 1 << p.s, M2 = M * M;
+    int rt = std::min(nrhs, sizeof(R) == 4 ? 32 : 8);
+    auto bytes = [&](int rt_) { return (rt_ * M2 + Q2 + M2 + rt_ * Q2 + rt_ * M * Q) * (int)sizeof(CT); };
+    while (bytes(rt) > p.smem_optin && rt > 1) rt--;
+    if (bytes(rt) > p.smem_optin) return (int)cudaErrorInvalidConfiguration;
+    const long long nA = 1LL << (2 * p.l1);
+    const Geom g = geom(p.l1, rt, 1, nA);
+    dim3 grid((unsigned)nA, (unsigned)((nrhs + rt - 1) / rt));
+    if (count_only) return check();
+    auto k = k_term<R, Q>;
+    set_smem(k, p.smem_optin);
+    k<<<grid, kThreads, bytes(rt), st>>>(p.tb, p.ph, g, vmat(), in, u);
+    return check();
+  }
+
+  int term_adj(const CT *g_in, CT *out) {
+    const int M = 1 << p.s, M2 = M * M;
+    int rt = std::min(nrhs, sizeof(R) == 4 ? 32 : 8);
+    auto bytes = [&](int rt_) { return (2 * rt_ * M2 + M2 + Q2 + rt_ * Q * M) * (int)sizeof(CT); };
+    while (bytes(rt) > p.smem_optin && rt > 1) rt--;
+    if (bytes(rt) > p.smem_optin) return (int)cudaErrorInvalidConfiguration;
+    const long long nA = 1LL << (2 * p.l1);
+    const Geom g = geom(p.l1, rt, 1, nA);
+    dim3 grid((unsigned)nA, (unsigned)((nrhs + rt - 1) / rt));
+    if (count_only) return check();
+    auto k = k_term_adj<R, Q>;
+    set_smem(k, p.smem_optin);
+    k<<<grid, kThreads, bytes(rt), st>>>(p.tb, p.ph, g, vmat(), g_in, out);
+    return check();
+  }
+
+  // Forward apply; stop_stage >= 0 stops after that stage and leaves its state in *stage_out.
+  int forward(const void *f, void *u, int stop_stage, const void **stage_out) {
+    CT *S[2] = {(CT *)p.state[0], (CT *)p.state[1]};
+    int cur = 0, stage = 0, rc;
+    if ((rc = init((const CT *)f, S[cur]))) return rc;
+    if (stop_stage == stage) return *stage_out = S[cur], 0;
+    for (int l = p.l0 + 1; l <= p.lm; l++) {
+      if ((rc = trans<true, true>(l, S[cur], S[cur ^ 1]))) return rc;
+      cur ^= 1;
+      if (stop_stage == ++stage) return *stage_out = S[cur], 0;
+    }
+    if ((rc = sw<true>(S[cur], S[cur ^ 1]))) return rc;
+    cur ^= 1;
+    if (stop_stage == ++stage) return *stage_out = S[cur], 0;
+    for (int l = p.lm + 1; l <= p.l1; l++) {
+      if ((rc = trans<false, true>(l, S[cur], S[cur ^ 1]))) return rc;
+      cur ^= 1;
+      if (stop_stage == ++stage) return *stage_out = S[cur], 0;
+    }
+    return term(S[cur], (CT *)u);
+  }
+
+  // Adjoint apply: the forward steps conjugate-transposed, in reverse order.
+  int adjoint(const void *g, void *fbar) {
+    CT *S[2] = {(CT *)p.state[0], (CT *)p.state[1]};
+    int cur = 0, rc;
+    if ((rc = term_adj((const CT *)g, S[cur]))) return rc;
+    for (int l = p.l1; l >= p.lm + 1; l--) {
+      if ((rc = trans<true, false>(l, S[cur], S[cur ^ 1]))) return rc;
+      cur ^= 1;
+    }
+    if ((rc = sw<false>(S[cur], S[cur ^ 1]))) return rc;
+    cur ^= 1;
+    for (int l = p.lm; l >= p.l0 + 1; l--) {
+      if ((rc = trans<false, false>(l, S[cur], S[cur ^ 1]))) return rc;
+      cur ^= 1;
+    }
+    return init_adj(S[cur], (CT *)fbar);
+  }
+};
+
+// Widen one stage snapshot to complex128 in canonical order (RHS 0 of an nrhs=1 run).
+template <typename V> __global__ void k_to_c128(const V *__restrict__ in, double2 *__restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+template <typename R, int Q>
+int run_plan(const PlanDev &p, int kind, const void *in, void *out, int nrhs, cudaStream_t st, int stop_stage,
+             int *launches) {
+  const bool count = kind == RUN_COUNT_FWD || kind == RUN_COUNT_ADJ;
+  Runner<R, Q> r(p, st, nrhs, count);
+  int rc;
+  if (kind == RUN_FWD || kind == RUN_COUNT_FWD) {
+    const void *snap = nullptr;
+    rc = r.forward(in, out, stop_stage, &snap);
+    if (rc == 0 && stop_stage >= 0 && !count) {
+      const long long n = ((long long)p.N * p.N * Q * Q) << p.e;
+      k_to_c128<typename C2<R>::T><<<592, 256, 0, st>>>((const typename C2<R>::T *)snap, (double2 *)out, n);
+      rc = (int)cudaGetLastError();
+    }
+  } else {
+    rc = r.adjoint(in, out);
+  }
+  if (launches) *launches = r.launches;
+  return rc;
+}
+
+}  // namespace fio

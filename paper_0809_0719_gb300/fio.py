@@ -1,0 +1,170 @@
+"""Thin Python binding of the C ABI in include/fio.h (argument marshalling only).
+
+Every step of the butterfly runs in the CUDA library libfio.so; this module only
+checks tensor shapes, dtypes and devices, passes raw pointers and the current
+CUDA stream, and turns status codes into exceptions.  There is no CPU path: if
+the library cannot be built or loaded, every call raises.
+
+Operator (Candes, Demanet & Ying 2008, eq. dfio): u(x) = sum_k e^{2 pi i Phi(x,k)} f(k)
+on N x N grids.  Tensors are (nrhs, N, N) complex (complex128 for precision
+"f64", complex64 for "f32"); f[r, k1 + N/2, k2 + N/2] is the source at k,
+u[r, i1, i2] the potential at x = (i1/N, i2/N).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+FIO_OK, FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ETIMEOUT, FIO_EDEVICE = 0, -1, -2, -3, -4, -5
+F64, F32 = 0, 1
+PHASES = {"linear": 0, "ellipse": 1, "circle": 2, "separable": 3}
+PRECISIONS = {"f64": F64, "f32": F32}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libfio.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class FIOError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("fio status %d: %s" % (code, msg))
+        self.code = code
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("N", "L", "q", "s", "e", "l0", "lm", "l1", "phase_id", "precision",
+                                            "nrhs_max", "nstages")] + [
+        ("pairs_per_level", ctypes.c_longlong), ("state_bytes", ctypes.c_longlong),
+        ("table_bytes", ctypes.c_longlong), ("max_box_sources", ctypes.c_int)]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfio.so, building it first (nvcc, sm_103a) if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, ip = ctypes.c_void_p, ctypes.c_int
+            L.fio_plan.argtypes = [ctypes.POINTER(vp), ip, ip, ip, ctypes.POINTER(ctypes.c_double), ip, ip, ip, ip, ip]
+            L.fio_destroy.argtypes = [vp]
+            L.fio_apply.argtypes = [vp, vp, vp, ip, vp]
+            L.fio_apply_adjoint.argtypes = [vp, vp, vp, ip, vp]
+            L.fio_apply_host.argtypes = [vp, vp, vp, ip, ip, vp]
+            L.fio_debug_stage.argtypes = [vp, vp, ip, vp, vp]
+            L.fio_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+            L.fio_kernel_launches.argtypes = [vp, ip, ip]
+            L.fio_last_error.restype = ctypes.c_char_p
+            _lib = L
+        return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != FIO_OK:
+        raise FIOError(rc, lib().fio_last_error().decode())
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A butterfly plan: fio_plan(N, q, phase, params, precision, nrhs_max, s, e)."""
+
+    def __init__(self, N: int, q: int, phase="ellipse", params=(2.0, 1.0, 16.0, 1.0), precision="f32",
+                 nrhs_max: int = 1, s: int = -1, e: int = -1):
+        self._h = None
+        L = lib()
+        pid = PHASES[phase] if isinstance(phase, str) else int(phase)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        prm = [] if pid == 0 else list(params)
+        arr = (ctypes.c_double * max(1, len(prm)))(*prm)
+        h = ctypes.c_void_p()
+        _check(L.fio_plan(ctypes.byref(h), N, q, pid, arr, len(prm), prec, nrhs_max, s, e))
+        self._h = h
+        self.info = PlanInfo()
+        _check(L.fio_plan_info(h, ctypes.byref(self.info)))
+        self.N, self.q = N, q
+        self.dtype = torch.complex128 if prec == F64 else torch.complex64
+
+    def close(self) -> None:
+        if self._h is not None and _lib is not None:
+            _lib.fio_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev_tensor(self, x: torch.Tensor, name: str) -> torch.Tensor:
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+        if x.dtype != self.dtype:
+            raise TypeError("%s must be %s for this plan, got %s" % (name, self.dtype, x.dtype))
+        if x.dim() == 2:
+            x = x.unsqueeze(0)
+        if x.shape[-2:] != (self.N, self.N):
+            raise ValueError("%s must have shape (nrhs, %d, %d), got %s" % (name, self.N, self.N, tuple(x.shape)))
+        return x.contiguous()
+
+    def apply(self, f: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """u = B f (fio_apply) on the current (or given) CUDA stream."""
+        f = self._dev_tensor(f, "f")
+        u = torch.empty_like(f) if out is None else out
+        _check(lib().fio_apply(self._h, f.data_ptr(), u.data_ptr(), f.shape[0], _stream_ptr(stream)))
+        return u
+
+    def adjoint(self, g: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """fbar = B^H g (fio_apply_adjoint)."""
+        g = self._dev_tensor(g, "g")
+        fb = torch.empty_like(g) if out is None else out
+        _check(lib().fio_apply_adjoint(self._h, g.data_ptr(), fb.data_ptr(), g.shape[0], _stream_ptr(stream)))
+        return fb
+
+    def apply_host(self, x: torch.Tensor, out: torch.Tensor, adjoint: bool = False, stream=None) -> torch.Tensor:
+        """fio_apply_host: host (ideally pinned) input and output; copies happen inside the call."""
+        if x.is_cuda or out.is_cuda or x.dtype != self.dtype or out.dtype != self.dtype:
+            raise TypeError("apply_host takes CPU tensors of dtype %s" % self.dtype)
+        if not (x.is_contiguous() and out.is_contiguous()):
+            raise ValueError("apply_host needs contiguous tensors")
+        n = x.shape[0] if x.dim() == 3 else 1
+        _check(lib().fio_apply_host(self._h, x.data_ptr(), out.data_ptr(), n, int(adjoint), _stream_ptr(stream)))
+        return out
+
+    def debug_stage(self, f: torch.Tensor, stage: int, stream=None) -> torch.Tensor:
+        """State after `stage` as complex128 (a1, a2, b1, b2, t1, t2) (fio_debug_stage, RHS 0 of f)."""
+        f = self._dev_tensor(f, "f")[:1].contiguous()
+        out = torch.empty(self.info.pairs_per_level * self.q * self.q, dtype=torch.complex128, device=f.device)
+        _check(lib().fio_debug_stage(self._h, f.data_ptr(), stage, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def kernel_launches(self, nrhs: int, adjoint: bool = False) -> int:
+        return int(lib().fio_kernel_launches(self._h, nrhs, int(adjoint)))
+
+
+class FIOFunction(torch.autograd.Function):
+    """u = B f with backward grad_f = B^H grad_u (the hand-written adjoint butterfly)."""
+
+    @staticmethod
+    def forward(ctx, f, plan):
+        ctx.plan = plan
+        return plan.apply(f)
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        return ctx.plan.adjoint(grad_u.contiguous()), None
+
+
+def fio_apply(f: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable apply."""
+    return FIOFunction.apply(f, plan)

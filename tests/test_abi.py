@@ -1,0 +1,69 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point
+declared in include/fio.h, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if hdr.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", hdr)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(fio_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0809_0719_gb300 import fio
+
+    return fio.lib()
+
+
+def test_header_declares_the_api():
+    names = header_functions()
+    for n in ("fio_plan", "fio_apply", "fio_apply_adjoint", "fio_destroy", "fio_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in header_functions():
+        assert hasattr(lib, n), n
+
+
+def test_plan_rejects_bad_arguments_without_a_gpu(lib):
+    h = ctypes.c_void_p()
+    prm = (ctypes.c_double * 4)(2, 1, 16, 1)
+    cases = [
+        (48, 5, 1, 4, 1, 1, -1, -1),    # N not a power of two
+        (2, 5, 1, 4, 1, 1, -1, -1),     # N too small
+        (64, 1, 1, 4, 1, 1, -1, -1),    # q < 2
+        (64, 4, 1, 4, 1, 1, -1, -1),    # q not compiled
+        (64, 5, 9, 4, 1, 1, -1, -1),    # unknown phase
+        (64, 5, 1, 3, 1, 1, -1, -1),    # wrong nparams
+        (64, 5, 1, 4, 7, 1, -1, -1),    # unknown precision
+        (64, 5, 1, 4, 1, 0, -1, -1),    # nrhs_max < 1
+        (64, 5, 1, 4, 1, 1, -1, 9),     # e too large
+    ]
+    for N, q, ph, npar, prec, nr, s, e in cases:
+        rc = lib.fio_plan(ctypes.byref(h), N, q, ph, prm, npar, prec, nr, s, e)
+        assert rc == -1, (N, q, ph, npar, prec, nr, s, e, rc)
+        assert len(lib.fio_last_error()) > 0
+
+
+def test_calls_on_null_plan_fail_cleanly(lib):
+    assert lib.fio_apply(None, None, None, 1, None) == -1
+    assert lib.fio_apply_adjoint(None, None, None, 1, None) == -1
+    assert lib.fio_destroy(None) == 0
+
+
+def test_binding_has_no_cpu_path():
+    # the binding's compute calls go through the library only
+    src = open(os.path.join(ROOT, "paper_0809_0719_gb300", "fio.py")).read()
+    assert "oracle" not in src and "numpy" not in src

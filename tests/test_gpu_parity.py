@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA butterfly against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances
+  FP64 form : relative L2 <= 1e-12 against the oracle butterfly with equal (q, s, e),
+              per stage and end to end (both sides take every integer decision --
+              the source-to-box assignment -- with the same FP64 expressions).
+  FP32 form : relative L2 <= 1e-5 against the oracle butterfly.  FP32 carries a unit
+              roundoff of 6e-8; each of the <= 2L steps multiplies by a Lagrange
+              operator of norm ~2-3 and adds a few roundings, and the FP32 sin/cos of
+              the FP64-reduced phase adds ~1e-7 per factor, so ~1e-6 is expected and
+              1e-5 (the floor of the stated FP32 accuracy bar) leaves a 10x margin.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_0809_0719_gb300.inputs import gaussian_batch, gaussian_sources, sample_indices
+
+pytestmark = pytest.mark.gpu
+
+ELL16 = (2.0, 1.0, 16.0, 1.0)
+CIRC20 = (3.0, 1.0, 20.0, 1.0)
+SEP = (0.3, 0.2, 0.25, 0.1)
+PH = {"ellipse": (1, ELL16), "circle": (2, CIRC20), "linear": (0, ()), "separable": (3, SEP)}
+
+F64_TOL = 1e-12
+F32_TOL = 1e-5
+
+_oracle_cache = {}
+
+
+@pytest.fixture(scope="module")
+def fio():
+    from paper_0809_0719_gb300 import fio as F
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    F.lib()
+    return F
+
+
+def oracle_bf(oracle, N, q, phase, f, s, e):
+    key = (N, q, phase, s, e, f.tobytes())
+    if key not in _oracle_cache:
+        pid, prm = PH[phase]
+        _oracle_cache[key] = oracle.butterfly(N, q, pid, list(prm), f, s=s, e=e)
+    return _oracle_cache[key]
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = [
+    # N, q, phase, s, e
+    (4, 3, "ellipse", 0, 0),
+    (8, 11, "ellipse", 0, 4),
+    (16, 3, "circle", 0, 0),
+    (32, 7, "ellipse", 3, 1),
+    (64, 5, "ellipse", 0, 2),
+    (64, 5, "ellipse", 3, 2),
+    (64, 9, "linear", 3, 2),
+    (64, 5, "separable", 3, 2),
+    (128, 5, "circle", 3, 2),
+    (128, 7, "ellipse", 3, 0),
+]
+
+
+@pytest.mark.parametrize("N,q,phase,s,e", CASES)
+@pytest.mark.parametrize("prec,nrhs", [("f64", 1), ("f64", 5), ("f32", 3), ("f32", 9)])
+def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, nrhs):
+    pid, prm = PH[phase]
+    plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
+    try:
+        F = gaussian_batch(N, range(100, 100 + nrhs))
+        f = torch.from_numpy(F).to(plan.dtype).cuda()
+        u = plan.apply(f).cpu().numpy()
+        torch.cuda.synchronize()
+        tol = F64_TOL if prec == "f64" else F32_TOL
+        for r in range(nrhs):
+            ref = oracle_bf(oracle, N, q, phase, F[r].astype(np.complex64).astype(np.complex128) if prec == "f32" else F[r],
+                            plan.info.s, e)
+            assert rel(u[r], ref) < tol, (r, rel(u[r], ref))
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("N,q,phase,s,e", [(64, 5, "ellipse", 0, 2), (128, 7, "circle", 3, 2), (32, 3, "separable", 0, 1)])
+@pytest.mark.parametrize("prec,nrhs", [("f64", 1), ("f64", 3), ("f32", 10)])
+def test_adjoint_matches_oracle_adjoint(fio, oracle, N, q, phase, s, e, prec, nrhs):
+    pid, prm = PH[phase]
+    plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
+    try:
+        G = gaussian_batch(N, range(200, 200 + nrhs))
+        g = torch.from_numpy(G).to(plan.dtype).cuda()
+        fb = plan.adjoint(g).cpu().numpy()
+        tol = F64_TOL if prec == "f64" else F32_TOL
+        for r in range(nrhs):
+            gr = G[r].astype(np.complex64).astype(np.complex128) if prec == "f32" else G[r]
+            ref = oracle.butterfly_adjoint(N, q, pid, list(prm), gr, s=plan.info.s, e=e)
+            assert rel(fb[r], ref) < tol, (r, rel(fb[r], ref))
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("N,q,s,e", [(64, 5, 0, 2), (128, 5, 3, 1), (32, 9, 3, 0)])
+def test_every_stage_matches_oracle(fio, oracle, N, q, s, e):
+    plan = fio.Plan(N, q, "ellipse", ELL16, "f64", nrhs_max=1, s=s, e=e)
+    try:
+        F = gaussian_sources(N, 7)
+        f = torch.from_numpy(F).cuda()
+        for st in range(plan.info.nstages):
+            got = plan.debug_stage(f, st).cpu().numpy()
+            _, ref = oracle.butterfly(N, q, 1, list(ELL16), F, s=plan.info.s, e=e, stage=st)
+            assert rel(got, ref) < F64_TOL, (st, rel(got, ref))
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
+@pytest.mark.parametrize("N,q,e", [(64, 5, 2), (256, 9, 2)])
+def test_dot_test(fio, prec, tol, N, q, e):
+    plan = fio.Plan(N, q, "ellipse", ELL16, prec, nrhs_max=2, e=e)
+    try:
+        f = torch.from_numpy(gaussian_batch(N, [1, 2])).to(plan.dtype).cuda()
+        g = torch.from_numpy(gaussian_batch(N, [3, 4])).to(plan.dtype).cuda()
+        Bf = plan.apply(f).to(torch.complex128)
+        Bg = plan.adjoint(g).to(torch.complex128)
+        for r in range(2):
+            a = torch.vdot(g[r].to(torch.complex128).flatten(), Bf[r].flatten())
+            b = torch.vdot(Bg[r].flatten(), f[r].to(torch.complex128).flatten())
+            assert abs(a - b).item() < tol * abs(a).item()
+    finally:
+        plan.close()
+
+
+def test_zero_input_gives_zero_and_linearity(fio):
+    N = 64
+    plan = fio.Plan(N, 5, "ellipse", ELL16, "f64", nrhs_max=3)
+    try:
+        z = torch.zeros(1, N, N, dtype=torch.complex128, device="cuda")
+        assert plan.apply(z).abs().max().item() == 0.0
+        F = torch.from_numpy(gaussian_batch(N, [5, 6])).cuda()
+        a, b = 0.3 - 1.1j, 2.0 + 0.5j
+        comb = torch.stack([F[0], F[1], a * F[0] + b * F[1]])
+        U = plan.apply(comb)
+        assert (U[2] - (a * U[0] + b * U[1])).abs().max().item() < 1e-12 * U.abs().max().item()
+    finally:
+        plan.close()
+
+
+def test_nrhs_batch_equals_single_calls(fio):
+    N = 64
+    plan = fio.Plan(N, 7, "circle", CIRC20, "f32", nrhs_max=11)
+    try:
+        F = torch.from_numpy(gaussian_batch(N, range(11))).to(torch.complex64).cuda()
+        U = plan.apply(F)
+        for r in (0, 7, 10):
+            assert torch.equal(plan.apply(F[r:r + 1])[0], U[r])
+    finally:
+        plan.close()
+
+
+def test_apply_host_matches_device(fio):
+    N = 128
+    plan = fio.Plan(N, 5, "ellipse", ELL16, "f32", nrhs_max=4)
+    try:
+        F = torch.from_numpy(gaussian_batch(N, range(4))).to(torch.complex64)
+        dev = plan.apply(F.cuda()).cpu()
+        out = torch.empty_like(F).pin_memory()
+        plan.apply_host(F.pin_memory(), out)
+        assert torch.equal(out, dev)
+        gb = plan.adjoint(F.cuda()).cpu()
+        plan.apply_host(F.pin_memory(), out, adjoint=True)
+        assert torch.equal(out, gb)
+    finally:
+        plan.close()
+
+
+def test_bad_arguments_raise(fio):
+    plan = fio.Plan(64, 5, "ellipse", ELL16, "f32", nrhs_max=2)
+    try:
+        with pytest.raises(fio.FIOError):
+            plan.apply(torch.zeros(3, 64, 64, dtype=torch.complex64, device="cuda"))
+        with pytest.raises(TypeError):
+            plan.apply(torch.zeros(1, 64, 64, dtype=torch.complex128, device="cuda"))
+        with pytest.raises(fio.FIOError):
+            plan.debug_stage(torch.zeros(1, 64, 64, dtype=torch.complex64, device="cuda"), 99)
+    finally:
+        plan.close()
+    for kw in (dict(N=96, q=5), dict(N=64, q=4), dict(N=64, q=5, e=5)):
+        with pytest.raises(fio.FIOError):
+            fio.Plan(kw.pop("N"), kw.pop("q"), "ellipse", ELL16, "f32", **kw)
+
+
+def test_autograd_backward_is_adjoint(fio):
+    N = 64
+    plan = fio.Plan(N, 5, "ellipse", ELL16, "f64", nrhs_max=1)
+    try:
+        f = torch.from_numpy(gaussian_sources(N, 8))[None].cuda().requires_grad_(True)
+        ustar = torch.from_numpy(gaussian_sources(N, 9))[None].cuda()
+        loss = (fio.fio_apply(f, plan) - ustar).abs().pow(2).sum()
+        loss.backward()
+        with torch.no_grad():
+            ref = 2.0 * plan.adjoint(plan.apply(f) - ustar)
+        assert (f.grad - ref).abs().max().item() < 1e-12 * ref.abs().max().item()
+    finally:
+        plan.close()
+
+
+def test_accuracy_against_direct_sum_medium(fio, oracle):
+    # both forms against eq. dfio on sampled x; the FP32 form meets max(2 x FP64 error, 1e-5).
+    # At q=9 the oracle butterfly's own error for this phase is ~4e-6 (Sec. 5 behaviour).
+    N, q = 256, 9
+    F = gaussian_sources(N, 1)
+    xi = sample_indices(N, 512, 1000)
+    ref = oracle.direct(N, 1, list(ELL16), F, xi)
+    errs = {}
+    for prec in ("f64", "f32"):
+        plan = fio.Plan(N, q, "ellipse", ELL16, prec, nrhs_max=1)
+        try:
+            u = plan.apply(torch.from_numpy(F).to(plan.dtype).cuda()).cpu().numpy().reshape(-1)
+            errs[prec] = rel(u[xi], ref)
+        finally:
+            plan.close()
+    assert errs["f64"] < 3e-5
+    assert errs["f32"] <= max(2 * errs["f64"], 1e-5)
