@@ -1,0 +1,376 @@
+"""Benchmark: butterfly FIO apply on one GB300 (or N independent replicas).
+
+Workload (one "step" = one fio_apply of the whole path: initialization,
+recursion in p, switch, recursion in x, termination):
+  N = 1024, q = 9, ellipse phase [2, 1, 16, 1] (eq. ex1 with the constants scaled by 1/16),
+  32 right-hand sides of complex64 white noise (seeds 0..31), FP32 form, s = 3, e = 2.
+The FP64 form (1 RHS, same N and q) is timed beside it.  The JSON line reports
+outputs/s = N^2 * nrhs / time, the rel-L2 error against the FP64 direct sum on
+512 seeded x, per-kernel times and the dominant kernel's roofline, the same
+metric end to end through host buffers, and the CPU oracle timed on the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torchrun; every rank runs an independent replica (the
+butterfly of one operator does not shard without an all-to-all; replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FIO outputs/s (N²·RHS/s) at N=1024 q=9, FP32 vs FP64 form; rel-L2 err"
+N, Q, NRHS, S, E = 1024, 9, 32, 3, 2
+PARAMS = (2.0, 1.0, 16.0, 1.0)
+NSAMPLE = 512
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"
+FP32_PEAK = 152 * 128 * 2 * 2.070e9
+
+
+def workload_config(precision="f32", nrhs=NRHS):
+    return {"workload": "2D butterfly FIO apply N=%d q=%d ellipse[2,1,16,1] %d RHS %s form s=%d e=%d"
+                        % (N, Q, nrhs, precision.upper(), S, E),
+            "N": N, "q": Q, "nrhs": nrhs, "precision": precision, "s": S, "e": E, "phase": "ellipse/16",
+            "l2": "inputs larger than L2: state 87 GB per level, no flush needed"}
+
+
+# ------------------------------------------------------------------ helpers
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_flops_bytes(kind: str, info, nrhs: int) -> tuple[float, float]:
+    """Algorithmic FP32 flops and HBM bytes of ONE launch of a kernel kind.
+
+    Per pair (A,B) and RHS: translations 24q^3 + 30q^2 flops (6q^3 complex x real
+    MACs of the dimension-wise Lagrange sums, 5q^2 complex modulations); switch
+    8q^4 (a q^2 x q^2 complex matrix-vector product); termination
+    4Mq^2 + 4M^2 q + 6(M^2 + q^2) with M = 2^s; initialization 4q^2 + 8 per
+    source, box A and RHS.  Bytes: the state read and written once (complex,
+    8 B in FP32) plus f or u.  Phase evaluations are not counted here."""
+    q, M = info.q, 1 << info.s
+    P = info.pairs_per_level
+    eb = 8 if info.precision == 1 else 16
+    blk = P * nrhs * q * q * eb
+    NN = info.N * info.N
+    if kind.startswith("trans"):
+        return P * nrhs * (24 * q ** 3 + 30 * q ** 2), 2 * blk
+    if kind.startswith("switch"):
+        return P * nrhs * 8 * q ** 4, 2 * blk
+    if kind.startswith("term"):
+        return P * nrhs * (4 * M * q * q + 4 * M * M * q + 6 * (M * M + q * q)), blk + NN * nrhs * eb
+    if kind.startswith("init"):
+        return (4 ** info.l0) * NN * nrhs * (4 * q * q + 8), blk + NN * nrhs * eb
+    return 0.0, 0.0
+
+
+def time_steps(fn, steps, warmup, torch):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def cpu_baseline(f0: np.ndarray, nsample: int):
+    """The FP64 CPU oracle as it stands: the direct sum of eq. dfio on a seeded
+    sample of x of RHS 0 of the workload, all host threads.  Returns the timing
+    record and the sampled reference values (used for the rel-L2 errors)."""
+    from oracle import oracle as O
+    from paper_0809_0719_gb300.inputs import sample_indices
+
+    xi = sample_indices(N, nsample, 1000)
+    t0 = time.perf_counter()
+    ref = O.direct(N, O.ELLIPSE, list(PARAMS), f0, xi)
+    dt = time.perf_counter() - t0
+    rec = {"value": nsample / dt, "unit": "outputs/s", "cores": O.threads(), "kind": "oracle",
+           "sample": "FP64 direct sum (eq. dfio) at %d seeded x of RHS 0 of the N=%d workload, %.1f s wall"
+                     % (nsample, N, dt)}
+    return rec, xi, ref
+
+
+def rel_err(u, xi, ref):
+    a = u.reshape(-1)[xi].astype(np.complex128)
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+# ------------------------------------------------------------------ arms
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle, as it stands, on this host's cores."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_0809_0719_gb300.inputs import gaussian_sources, sample_indices
+
+    O.build()
+    f0 = gaussian_sources(N, 0)
+    nsample = 128
+    times = []
+    for it in range(args.warmup + args.steps):
+        xi = sample_indices(N, nsample, 2000 + it)
+        t0 = time.perf_counter()
+        O.direct(N, O.ELLIPSE, list(PARAMS), f0, xi)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = nsample / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "outputs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": v, "unit": "outputs/s", "cores": O.threads(), "kind": "oracle",
+                             "sample": "FP64 direct sum at %d seeded x per step of RHS 0, N=%d" % (nsample, N)},
+            "e2e": {"value": v, "unit": "outputs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_0809_0719_gb300 import fio
+    from paper_0809_0719_gb300.inputs import gaussian_batch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def tmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    F = gaussian_batch(N, range(NRHS))
+    # ---- FP32 form, 32 RHS (the headline)
+    plan = fio.Plan(N, Q, "ellipse", PARAMS, "f32", nrhs_max=NRHS, s=S, e=E)
+    f = torch.from_numpy(F).to(torch.complex64).to(dev)
+    u = torch.empty_like(f)
+    step = lambda: plan.apply(f, out=u)
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    plan.profile(True)
+    with ClockSampler(local) as clk:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            step()
+        b.record()
+        barrier()
+    plan.profile(False)
+    ms32 = tmax(a.elapsed_time(b) / args.steps)
+    prof = plan.profile_read()
+    launches_per_step = plan.kernel_launches(NRHS)
+    u32 = u[0].cpu().numpy()
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    fh = torch.from_numpy(F).to(torch.complex64).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    e2e_step = lambda: plan.apply_host(fh, uh)
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_ms = tmax((time.perf_counter() - t0) * 1e3 / args.steps)
+    info = plan.info
+    plan.close()
+    del f, u, fh, uh
+    torch.cuda.empty_cache()
+
+    # ---- FP64 form, 1 RHS, same N and q
+    plan64 = fio.Plan(N, Q, "ellipse", PARAMS, "f64", nrhs_max=1, s=S, e=E)
+    f64 = torch.from_numpy(F[:1]).to(dev)
+    u64 = torch.empty_like(f64)
+    ms64 = tmax(time_steps(lambda: plan64.apply(f64, out=u64), max(1, args.steps // 2), max(3, args.warmup // 2),
+                           torch))
+    u64h = u64[0].cpu().numpy()
+    plan64.close()
+
+    if rank != 0:
+        return
+    out32 = N * N * NRHS * world / (ms32 * 1e-3)
+    out64 = N * N * 1 * world / (ms64 * 1e-3)
+
+    # per-kernel breakdown and the dominant kernel's roofline
+    kernels = {}
+    for k, (n, ms) in prof.items():
+        fl, by = kernel_flops_bytes(k, info, NRHS)
+        avg = ms / n
+        kernels[k] = {"launches": n, "ms_per_launch": avg, "share": None, "gflops": fl / (avg * 1e-3) / 1e9,
+                      "gbs": by / (avg * 1e-3) / 1e9}
+    tot = sum(v["ms_per_launch"] * v["launches"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = v["ms_per_launch"] * v["launches"] / tot
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    fl, by = kernel_flops_bytes(dom, info, NRHS)
+    dom_ms = kernels[dom]["ms_per_launch"]
+    roof = {"kernel": dom, "bound": "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12,
+            "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s", "frac": fl / (dom_ms * 1e-3) / FP32_PEAK,
+            "traffic": None, "peak_source": FP32_PEAK_NOTE + " (derived, not measured)",
+            "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
+            "hbm_achieved_gbs": by / (dom_ms * 1e-3) / 1e9}
+    probes = {}
+    for kind in ("fp32", "fp64", "sfu"):
+        try:
+            probes[kind] = fio.peak_probe(kind)
+        except Exception as ex:  # measurement aid only
+            probes[kind] = str(ex)
+
+    base, xi, ref = cpu_baseline(F[0], NSAMPLE)
+    err32 = rel_err(u32, xi, ref)
+    err64 = rel_err(u64h, xi, ref)
+    line = {
+        "metric": METRIC, "value": out32, "unit": "outputs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (white-noise complex64 sources, seeds 0..31)",
+        "config": dict(workload_config(), parallelism="replicas" if world > 1 else "single GPU"),
+        "rel_l2_err": err32,
+        "fp64_form": {"value": out64, "unit": "outputs/s", "ms_per_step": ms64, "nrhs": 1, "dtype": "f64",
+                      "rel_l2_err": err64},
+        "speedup_f32_vs_f64_form": out32 / out64,
+        "accuracy_bar_met": err32 <= max(2 * err64, 1e-5),
+        "e2e": {"value": N * N * NRHS * world / (e2e_ms * 1e-3), "unit": "outputs/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": N * N * NRHS * 8, "d2h_bytes_per_step": N * N * NRHS * 8,
+                "api": "fio_apply_host (pinned host buffers)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "kernels": kernels,
+        "roofline": roof,
+        "peak_probes": probes,
+        "cpu_baseline": base,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_small(args):
+    """--case small: only the timed applies of an N=256, q=9, 8-RHS FP32 plan (a few GB),
+    forward then adjoint; the case the ncu captures use."""
+    import torch
+
+    from paper_0809_0719_gb300 import fio
+    from paper_0809_0719_gb300.inputs import gaussian_batch
+
+    n, r = 256, 8
+    plan = fio.Plan(n, Q, "ellipse", PARAMS, "f32", nrhs_max=r, s=S, e=E)
+    f = torch.from_numpy(gaussian_batch(n, range(r))).to(torch.complex64).cuda()
+    u = torch.empty_like(f)
+    ms = time_steps(lambda: plan.apply(f, out=u), args.steps, args.warmup, torch)
+    msa = time_steps(lambda: plan.adjoint(u, out=f), args.steps, args.warmup, torch)
+    print(json.dumps({"case": "small", "N": n, "q": Q, "nrhs": r, "ms_forward": ms, "ms_adjoint": msa,
+                      "launches_per_apply": plan.kernel_launches(r)}), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: N=256 q=9 8-RHS applies only (for profiler captures)")
+    args = ap.parse_args()
+    if args.case == "small":
+        run_small(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -137,6 +137,28 @@ int fio_plan_info(fio_plan_t plan, fio_plan_info_t *info);
  * with nrhs right-hand sides enqueues. */
 int fio_kernel_launches(fio_plan_t plan, int nrhs, int adjoint);
 
+/* Per-kernel timing.  fio_profile(plan, 1) clears the counters and starts
+ * recording a CUDA event pair on the launch stream around every kernel that
+ * fio_apply* enqueues with this plan (at most 4096 launches); fio_profile(plan, 0)
+ * stops.  fio_profile_read synchronises on the recorded events and fills up to
+ * max entries {name, launches, total ms} for the kernel kinds that ran, setting
+ * *n to their number.  Kinds: init, trans_p (eq. alg2b), switch (eq. alg2m),
+ * trans_x (eq. alg2c), term (eq. alg2d) and their conjugate transposes *_adj. */
+typedef struct {
+  char name[24];
+  long long launches;
+  double ms;
+} fio_kernel_time_t;
+int fio_profile(fio_plan_t plan, int enable);
+int fio_profile_read(fio_plan_t plan, fio_kernel_time_t *out, int max, int *n);
+
+/* fio_peak_probe -- measure a per-GPU arithmetic peak on the current device:
+ * kind 0 FP32 FMA, 1 FP64 FMA (returned as flop/s, 2 per FMA), 2 FP32 sin/cos
+ * through the special-function unit (results/s).  A fixed dependent-chain
+ * kernel over every SM, timed with CUDA events; synchronises the device.
+ * The paper has no counterpart: it is a measurement aid for the roofline. */
+int fio_peak_probe(int kind, double *per_second);
+
 /* fio_last_error -- thread-local message of the last failing call ("" if none). */
 const char *fio_last_error(void);
 

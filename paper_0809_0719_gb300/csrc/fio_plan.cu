@@ -342,6 +342,10 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
 int fio_destroy(fio_plan_t p) {
   if (!p) return FIO_OK;
   cudaDeviceSynchronize();
+  if (p->d.prof) {
+    for (int i = 0; i < 2 * fio::kProfSlots; i++) cudaEventDestroy(p->d.prof->ev[i]);
+    delete p->d.prof;
+  }
   cudaFree(p->d.state[0]);
   cudaFree(p->d.state[1]);
   cudaFree(p->tables);
@@ -429,6 +433,60 @@ int fio_plan_info(fio_plan_t p, fio_plan_info_t *info) {
   info->state_bytes = p->state_bytes;
   info->table_bytes = p->table_bytes;
   info->max_box_sources = d.maxsrc;
+  return FIO_OK;
+}
+
+int fio_profile(fio_plan_t p, int enable) {
+  if (!p) return fail(FIO_EINVAL, "plan is NULL");
+  int rc = check_device(p);
+  if (rc) return rc;
+  if (!p->d.prof) {
+    fio::Prof *pr = new (std::nothrow) fio::Prof();
+    if (!pr) return fail(FIO_ENOMEM, "host allocation failed");
+    for (int i = 0; i < 2 * fio::kProfSlots; i++) {
+      cudaError_t ce = cudaEventCreate(&pr->ev[i]);
+      if (ce != cudaSuccess) {
+        for (int j = 0; j < i; j++) cudaEventDestroy(pr->ev[j]);
+        delete pr;
+        return cuda_fail(ce, "cudaEventCreate");
+      }
+    }
+    p->d.prof = pr;
+  }
+  fio::Prof *pr = p->d.prof;
+  if (enable) {
+    pr->n = 0;
+    for (int k = 0; k < fio::kKinds; k++) {
+      pr->ms[k] = 0;
+      pr->launches[k] = 0;
+    }
+  }
+  pr->enabled = enable ? 1 : 0;
+  return FIO_OK;
+}
+
+int fio_profile_read(fio_plan_t p, fio_kernel_time_t *out, int max, int *n) {
+  if (!p || !out || !n) return fail(FIO_EINVAL, "NULL argument");
+  *n = 0;
+  fio::Prof *pr = p->d.prof;
+  if (!pr) return FIO_OK;
+  for (int i = 0; i < pr->n; i++) {
+    cudaError_t ce = cudaEventSynchronize(pr->ev[2 * i + 1]);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventSynchronize");
+    float ms = 0.f;
+    if ((ce = cudaEventElapsedTime(&ms, pr->ev[2 * i], pr->ev[2 * i + 1])) != cudaSuccess)
+      return cuda_fail(ce, "cudaEventElapsedTime");
+    pr->ms[pr->kind[i]] += ms;
+    pr->launches[pr->kind[i]]++;
+  }
+  pr->n = 0;
+  for (int k = 0; k < fio::kKinds && *n < max; k++) {
+    if (!pr->launches[k]) continue;
+    fio_kernel_time_t &o = out[(*n)++];
+    snprintf(o.name, sizeof o.name, "%s", fio::kKernelNames[k]);
+    o.launches = pr->launches[k];
+    o.ms = pr->ms[k];
+  }
   return FIO_OK;
 }
 

@@ -7,6 +7,25 @@
 
 namespace fio {
 
+// Per-kernel timing with CUDA events recorded on the launch stream around each
+// launch (enabled by fio_profile).  Kinds index kKernelNames.
+constexpr int kKinds = 10;
+constexpr int kProfSlots = 4096;
+enum KernelKind {
+  K_INIT = 0, K_TRANS_P = 1, K_SWITCH = 2, K_TRANS_X = 3, K_TERM = 4,
+  K_TERM_ADJ = 5, K_TRANS_P_ADJ = 6, K_SWITCH_ADJ = 7, K_TRANS_X_ADJ = 8, K_INIT_ADJ = 9
+};
+static const char *const kKernelNames[kKinds] = {"init", "trans_p", "switch", "trans_x", "term",
+                                                 "term_adj", "trans_x_adj", "switch_adj", "trans_p_adj", "init_adj"};
+struct Prof {
+  int enabled;
+  int n;                        // events used
+  cudaEvent_t ev[2 * kProfSlots];
+  int kind[kProfSlots];
+  double ms[kKinds];
+  long long launches[kKinds];
+};
+
 // Everything a run needs from a plan (plain data, no ownership).
 struct PlanDev {
   Tables tb;
@@ -16,6 +35,7 @@ struct PlanDev {
   double T[2][kQMax][kQMax];
   double V[kMMax][kQMax];
   int smem_optin;
+  Prof *prof;  // NULL unless profiling was ever enabled
 };
 
 enum RunKind { RUN_FWD = 0, RUN_ADJ = 1, RUN_COUNT_FWD = 2, RUN_COUNT_ADJ = 3 };
@@ -65,9 +85,19 @@ template <typename R, int Q> struct Runner {
   }
   long long nb_at(int lb) const { return (1LL << lb) << (lb + p.e); }
 
+  int slot = -1;
+  void pre(int kind) {
+    slot = -1;
+    Prof *pr = p.prof;
+    if (count_only || !pr || !pr->enabled || pr->n >= kProfSlots) return;
+    slot = pr->n++;
+    pr->kind[slot] = kind;
+    cudaEventRecord(pr->ev[2 * slot], st);
+  }
   int check() {
     launches++;
     if (count_only) return 0;
+    if (slot >= 0) cudaEventRecord(p.prof->ev[2 * slot + 1], st);
     cudaError_t err = cudaGetLastError();
     return err == cudaSuccess ? 0 : (int)err;
   }
@@ -83,6 +113,7 @@ template <typename R, int Q> struct Runner {
     dim3 grid((unsigned)((nunits + U - 1) / U), (unsigned)((nrhs + rt - 1) / rt));
     const int smem = U * per_unit;
     if (count_only) return check();
+    pre(TYPE_P ? (FWD ? K_TRANS_P : K_TRANS_P_ADJ) : (FWD ? K_TRANS_X : K_TRANS_X_ADJ));
     if (TYPE_P) {
       auto k = k_trans_p<R, Q, FWD>;
       set_smem(k, p.smem_optin);
@@ -106,6 +137,7 @@ template <typename R, int Q> struct Runner {
     const Geom g = geom(p.lm, rt, U, pairs);
     dim3 grid((unsigned)((pairs + U - 1) / U), (unsigned)((nrhs + rt - 1) / rt));
     if (count_only) return check();
+    pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
     auto k = k_switch<R, Q, FWD>;
     set_smem(k, p.smem_optin);
     k<<<grid, kThreads, smem, st>>>(p.tb, p.ph, g, TC, in, out);
@@ -125,6 +157,7 @@ template <typename R, int Q> struct Runner {
     const Geom g = geom(p.l0, rt, 1, p.nbox_init);
     dim3 grid((unsigned)p.nbox_init, (unsigned)((nrhs + rt - 1) / rt));
     if (count_only) return check();
+    pre(K_INIT);
     auto k = k_init<R, Q>;
     set_smem(k, p.smem_optin);
     k<<<grid, kThreads, bytes(rt, GA), st>>>(p.tb, p.ph, g, ms, GA, f, out);
@@ -142,6 +175,7 @@ template <typename R, int Q> struct Runner {
     const Geom g = geom(p.l0, rt, 1, p.nbox_init);
     dim3 grid((unsigned)p.nbox_init, (unsigned)((nrhs + rt - 1) / rt));
     if (count_only) return check();
+    pre(K_INIT_ADJ);
     auto k = k_init_adj<R, Q>;
     set_smem(k, p.smem_optin);
     k<<<grid, kThreads, bytes(rt), st>>>(p.tb, p.ph, g, ms, in, fbar);
@@ -158,6 +192,7 @@ template <typename R, int Q> struct Runner {
     const Geom g = geom(p.l1, rt, 1, nA);
     dim3 grid((unsigned)nA, (unsigned)((nrhs + rt - 1) / rt));
     if (count_only) return check();
+    pre(K_TERM);
     auto k = k_term<R, Q>;
     set_smem(k, p.smem_optin);
     k<<<grid, kThreads, bytes(rt), st>>>(p.tb, p.ph, g, vmat(), in, u);
@@ -174,6 +209,7 @@ template <typename R, int Q> struct Runner {
     const Geom g = geom(p.l1, rt, 1, nA);
     dim3 grid((unsigned)nA, (unsigned)((nrhs + rt - 1) / rt));
     if (count_only) return check();
+    pre(K_TERM_ADJ);
     auto k = k_term_adj<R, Q>;
     set_smem(k, p.smem_optin);
     k<<<grid, kThreads, bytes(rt), st>>>(p.tb, p.ph, g, vmat(), g_in, out);

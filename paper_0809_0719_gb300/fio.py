@@ -35,6 +35,10 @@ class FIOError(RuntimeError):
         self.code = code
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double)]
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("N", "L", "q", "s", "e", "l0", "lm", "l1", "phase_id", "precision",
                                             "nrhs_max", "nstages")] + [
@@ -60,6 +64,9 @@ def lib() -> ctypes.CDLL:
             L.fio_debug_stage.argtypes = [vp, vp, ip, vp, vp]
             L.fio_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
             L.fio_kernel_launches.argtypes = [vp, ip, ip]
+            L.fio_profile.argtypes = [vp, ip]
+            L.fio_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ip, ctypes.POINTER(ip)]
+            L.fio_peak_probe.argtypes = [ip, ctypes.POINTER(ctypes.c_double)]
             L.fio_last_error.restype = ctypes.c_char_p
             _lib = L
         return _lib
@@ -150,6 +157,24 @@ class Plan:
 
     def kernel_launches(self, nrhs: int, adjoint: bool = False) -> int:
         return int(lib().fio_kernel_launches(self._h, nrhs, int(adjoint)))
+
+    def profile(self, enable: bool) -> None:
+        """fio_profile: start (clearing the counters) or stop per-kernel event timing."""
+        _check(lib().fio_profile(self._h, int(enable)))
+
+    def profile_read(self) -> dict:
+        """fio_profile_read: {kernel kind: (launches, total ms)} since profile(True)."""
+        buf = (KernelTime * 16)()
+        n = ctypes.c_int()
+        _check(lib().fio_profile_read(self._h, buf, 16, ctypes.byref(n)))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(n.value)}
+
+
+def peak_probe(kind: str) -> float:
+    """fio_peak_probe on the current device: 'fp32' / 'fp64' flop/s or 'sfu' sin/s."""
+    v = ctypes.c_double()
+    _check(lib().fio_peak_probe({"fp32": 0, "fp64": 1, "sfu": 2}[kind], ctypes.byref(v)))
+    return float(v.value)
 
 
 class FIOFunction(torch.autograd.Function):
