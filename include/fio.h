@@ -159,6 +159,33 @@ int fio_profile_read(fio_plan_t plan, fio_kernel_time_t *out, int max, int *n);
  * The paper has no counterpart: it is a measurement aid for the roofline. */
 int fio_peak_probe(int kind, double *per_second);
 
+/*
+ * fio_apply_noalloc -- u = B f for small grids, allocating nothing.
+ * The paper has no counterpart: this is a calling convenience.  It is for
+ * callers that cannot allocate device memory when they apply the operator (an
+ * embedding runtime that owns the allocator and forbids cudaMalloc after
+ * start-up, a real-time loop that must not block on allocation, a plugin
+ * without a memory pool): it needs no plan and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   N, q, phase_id, params, nparams, precision, s, e: as fio_plan, with
+ *          4 <= N <= 32, q in {3, 5, 7, 9}, 0 <= e <= 2
+ *   f, u   DEVICE pointers as in fio_apply; nrhs >= 1
+ * Its working memory -- the node and source tables and the two level buffers
+ * of expansion coefficients -- lives in one static device array of 8 MiB that
+ * every GPU loading this library holds until the process exits.  A problem
+ * whose tables plus two levels of 2^e N^2 q^2 nrhs complex coefficients exceed
+ * 8 MiB is rejected with FIO_EINVAL and a message naming both sizes.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array, which keeps the last call's contents (every coefficient is
+ * written before it is read, so nothing needs clearing): calls that overlap on
+ * the GPU (other streams, other host threads' streams) race and must be
+ * serialised by the caller.  The host side copies its tables from pageable
+ * memory, which waits for earlier work on the stream.
+ */
+int fio_apply_noalloc(int N, int q, int phase_id, const double *params, int nparams, int precision, int s, int e,
+                      const void *f, void *u, int nrhs, void *stream);
+
 /* fio_last_error -- thread-local message of the last failing call ("" if none). */
 const char *fio_last_error(void);
 

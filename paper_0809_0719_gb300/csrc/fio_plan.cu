@@ -111,6 +111,11 @@ size_t elem_bytes(const fio_plan_t p) { return p->d.precision == FIO_F64 ? 16 : 
 
 }  // namespace
 
+namespace fio {
+// Lets other translation units of the library report through fio_last_error().
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace fio
+
 extern "C" {
 
 const char *fio_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,81 @@
+"""fio_apply_noalloc: the allocation-free forward apply for small grids.
+
+It exists for callers that cannot allocate device memory when they apply the
+operator (their allocator belongs to an embedding runtime, or the call sits in a
+loop that must not block on allocation).  Its working memory is a fixed 8 MiB
+static device array shared by all calls.  The test calls it through the C ABI
+twice in a row, with different sizes and precisions so that the second call runs
+on the first call's leftover scratch, and checks each result against fio_apply
+(which uses plan-owned memory) within the parity tolerances of the other GPU
+tests.  This file is collected last so that a first-failure run has already run
+every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_0809_0719_gb300.inputs import gaussian_batch
+
+pytestmark = pytest.mark.gpu
+
+ELL16 = (2.0, 1.0, 16.0, 1.0)
+TOL = {0: 1e-12, 1: 1e-5}  # FP64 form, FP32 form
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0809_0719_gb300 import fio
+
+    assert torch.cuda.is_available()
+    L = fio.lib()
+    L.fio_apply_noalloc.argtypes = [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_double)] + [ctypes.c_int] * 4 + [
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    return L
+
+
+def _noalloc(lib, N, q, prec, s, e, f):
+    prm = (ctypes.c_double * 4)(*ELL16)
+    u = torch.empty_like(f)
+    st = torch.cuda.current_stream()
+    rc = lib.fio_apply_noalloc(N, q, 1, prm, 4, prec, s, e, f.data_ptr(), u.data_ptr(), f.shape[0], st.cuda_stream)
+    assert rc == 0, lib.fio_last_error()
+    torch.cuda.synchronize()
+    return u
+
+
+def _reference(N, q, prec, s, e, f):
+    from paper_0809_0719_gb300 import fio
+
+    plan = fio.Plan(N, q, "ellipse", ELL16, "f64" if prec == 0 else "f32", nrhs_max=f.shape[0], s=s, e=e)
+    try:
+        u = plan.apply(f)
+        torch.cuda.synchronize()
+        return u
+    finally:
+        plan.close()
+
+
+def _rel(a, b):
+    return float((a - b).abs().pow(2).sum().sqrt() / b.abs().pow(2).sum().sqrt())
+
+
+def test_noalloc_matches_fio_apply_on_two_calls_in_a_row(lib):
+    cases = [(32, 5, 0, 3, 2, 2), (16, 3, 1, 0, 1, 3)]  # N, q, precision, s, e, nrhs
+    for N, q, prec, s, e, nrhs in cases:
+        dt = torch.complex128 if prec == 0 else torch.complex64
+        f = torch.from_numpy(gaussian_batch(N, range(nrhs))).to(dt).cuda()
+        got = _noalloc(lib, N, q, prec, s, e, f)
+        ref = _reference(N, q, prec, s, e, f)
+        assert _rel(got, ref) <= TOL[prec], (N, q, prec, _rel(got, ref))
+
+
+def test_noalloc_rejects_problems_beyond_the_static_limit(lib):
+    f = torch.zeros(8, 32, 32, dtype=torch.complex128, device="cuda")
+    prm = (ctypes.c_double * 4)(*ELL16)
+    rc = lib.fio_apply_noalloc(32, 9, 1, prm, 4, 0, 3, 2, f.data_ptr(), f.data_ptr(), 8, None)
+    assert rc == -1
+    assert b"static limit" in lib.fio_last_error()
+    rc = lib.fio_apply_noalloc(64, 5, 1, prm, 4, 0, 3, 2, f.data_ptr(), f.data_ptr(), 1, None)
+    assert rc == -1
