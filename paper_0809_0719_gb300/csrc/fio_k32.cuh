@@ -1,0 +1,763 @@
+// fio_k32.cuh -- kernels of the FP32 form (coefficients, interpolation and
+// accumulation in FP32; phases in double-float on the FMA pipe, fio_df.cuh).
+//
+// Differences from the FP64-form kernels in fio_kernels.cuh:
+//  * one CTA owns a translation unit for up to 32 right-hand sides, so its
+//    20 q^2 phase factors are computed once and shared by all of them;
+//  * the CTA has 32 q threads and works on 8-RHS subtiles, which makes each
+//    pass of the dimension-wise Lagrange sums exactly one or two task rounds;
+//  * outputs are staged in shared memory and written as contiguous runs;
+//  * the switch evaluates G(x_t, p2_s) once per (t, s2) (q^3 per pair) and
+//    forms the q^4 kernel entries as rho(p1_s) G (homogeneity of Phi, Sec. 1).
+#pragma once
+#include "fio_df.cuh"
+#include "fio_kernels.cuh"
+
+namespace fio {
+
+constexpr int kRS = 8;      // RHS per subtile of a translation CTA
+constexpr int kRMax = 32;   // RHS per CTA (grid.y covers the rest)
+
+// df tables of an FP32-form plan (same indexing as the FP64 tables in Tables).
+struct TablesF {
+  const XNodeF *xnode;
+  const P1NodeF *p1node;
+  const P2NodeF *p2node;
+  const XNodeF *xgrid;
+  const SrcF *src;
+  PhaseF ph;
+};
+
+__device__ __forceinline__ const XNodeF &xnf(const Tables &tb, const TablesF &tf, int l, int box, int j, int q) {
+  return tf.xnode[tb.xoff[l] + box * (q + 1) + j];
+}
+__device__ __forceinline__ df rhof(const Tables &tb, const TablesF &tf, int j, int box, int t, int q) {
+  return tf.p1node[tb.p1off[j] + box * (q + 1) + t].rho;
+}
+__device__ __forceinline__ const P2NodeF &p2f(const Tables &tb, const TablesF &tf, int j, int box, int t, int q) {
+  return tf.p2node[tb.p2off[j] + box * (q + 1) + t];
+}
+
+// Phase family "centres": x at the centres of the four children A_sigma of A_p
+// (level l), p on the node grids of B (level lb) and of its children B_c (lb+1).
+//   ec[sigma][c][u] = e(x0(A_sigma), p^{B_c}_u)   (16 q^2)
+//   ep[sigma][t]    = e(x0(A_sigma), p^B_t)       (4 q^2)
+// scratch: >= 4 XDesc + 12 q df.
+template <int Q>
+__device__ void family_centres(const Tables &tb, const TablesF &tf, const Phase &ph, const UnitIdx &d, int l, int lb,
+                               float2 *ec, float2 *ep, unsigned char *scratch) {
+  constexpr int Q2 = Q * Q;
+  XDesc *xd = (XDesc *)scratch;
+  df *gc = (df *)(xd + 4);  // [4 sigma][2 c2][Q]
+  df *gp = gc + 8 * Q;      // [4 sigma][Q]
+  if (ph.id == 3) {  // separable test phase: direct FP64 evaluation
+    for (int idx = threadIdx.x; idx < 20 * Q2; idx += blockDim.x) {
+      const int sg = idx < 16 * Q2 ? idx / (4 * Q2) : (idx - 16 * Q2) / Q2;
+      const int a1 = 2 * d.ap1 + (sg >> 1), a2 = 2 * d.ap2 + (sg & 1);
+      const XNode &x1 = xn(tb, l, a1, Q, Q), &x2 = xn(tb, l, a2, Q, Q);
+      if (idx < 16 * Q2) {
+        const int c = (idx / Q2) & 3, u = idx % Q2;
+        ec[idx] = expi<float>(theta_xp(ph, x1, x2, pn1(tb, lb + 1, 2 * d.b1 + (c >> 1), u / Q, Q),
+                                       pn2(tb, lb + 1, 2 * d.b2 + (c & 1), u % Q, Q)));
+      } else {
+        const int t = (idx - 16 * Q2) % Q2;
+        ep[idx - 16 * Q2] = expi<float>(theta_xp(ph, x1, x2, pn1(tb, lb, d.b1, t / Q, Q), pn2(tb, lb, d.b2, t % Q, Q)));
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  if (threadIdx.x < 4) {
+    const int sg = threadIdx.x;
+    xd[sg] = xdesc(tf.ph, xnf(tb, tf, l, 2 * d.ap1 + (sg >> 1), Q, Q), xnf(tb, tf, l, 2 * d.ap2 + (sg & 1), Q, Q));
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 12 * Q; idx += blockDim.x) {
+    if (idx < 8 * Q) {
+      const int sg = idx / (2 * Q), c2 = (idx / Q) & 1, u2 = idx % Q;
+      gc[idx] = g_eval(tf.ph, xd[sg], p2f(tb, tf, lb + 1, 2 * d.b2 + c2, u2, Q));
+    } else {
+      const int k = idx - 8 * Q, sg = k / Q, t2 = k % Q;
+      gp[k] = g_eval(tf.ph, xd[sg], p2f(tb, tf, lb, d.b2, t2, Q));
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 20 * Q2; idx += blockDim.x) {
+    if (idx < 16 * Q2) {
+      const int sg = idx / (4 * Q2), c = (idx / Q2) & 3, u = idx % Q2;
+      const df rho = rhof(tb, tf, lb + 1, 2 * d.b1 + (c >> 1), u / Q, Q);
+      ec[idx] = expi_df(df_mul(rho, gc[(sg * 2 + (c & 1)) * Q + u % Q]));
+    } else {
+      const int k = idx - 16 * Q2, sg = k / Q2, t = k % Q2;
+      ep[k] = expi_df(df_mul(rhof(tb, tf, lb, d.b1, t / Q, Q), gp[sg * Q + t % Q]));
+    }
+  }
+  __syncthreads();
+}
+
+// Phase family "nodes": x on the node grids of A_sigma (level l) and A_p (l-1),
+// p at the centres of the children B_c (level lb+1).
+//   ea[sigma][c][t] = e(x^{A_sigma}_t, p0(B_c))   (16 q^2)
+//   eq[c][t']       = e(x^{A_p}_t', p0(B_c))       (4 q^2)
+// scratch: >= 5 q^2 XDesc + 10 q^2 df.
+template <int Q>
+__device__ void family_nodes(const Tables &tb, const TablesF &tf, const Phase &ph, const UnitIdx &d, int l, int lb,
+                             float2 *ea, float2 *eq, unsigned char *scratch) {
+  constexpr int Q2 = Q * Q;
+  XDesc *xd = (XDesc *)scratch;  // [4 sigma][Q2] then [Q2] for A_p
+  df *g = (df *)(xd + 5 * Q2);   // [5][Q2][2 c2]
+  if (ph.id == 3) {
+    for (int idx = threadIdx.x; idx < 20 * Q2; idx += blockDim.x) {
+      if (idx < 16 * Q2) {
+        const int sg = idx / (4 * Q2), c = (idx / Q2) & 3, t = idx % Q2;
+        const int a1 = 2 * d.ap1 + (sg >> 1), a2 = 2 * d.ap2 + (sg & 1);
+        ea[idx] = expi<float>(theta_xp(ph, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q),
+                                       pn1(tb, lb + 1, 2 * d.b1 + (c >> 1), Q, Q), pn2(tb, lb + 1, 2 * d.b2 + (c & 1), Q, Q)));
+      } else {
+        const int k = idx - 16 * Q2, c = k / Q2, t = k % Q2;
+        eq[k] = expi<float>(theta_xp(ph, xn(tb, l - 1, d.ap1, t / Q, Q), xn(tb, l - 1, d.ap2, t % Q, Q),
+                                     pn1(tb, lb + 1, 2 * d.b1 + (c >> 1), Q, Q), pn2(tb, lb + 1, 2 * d.b2 + (c & 1), Q, Q)));
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  for (int idx = threadIdx.x; idx < 5 * Q2; idx += blockDim.x) {
+    const int w = idx / Q2, t = idx % Q2;
+    if (w < 4)
+      xd[idx] = xdesc(tf.ph, xnf(tb, tf, l, 2 * d.ap1 + (w >> 1), t / Q, Q), xnf(tb, tf, l, 2 * d.ap2 + (w & 1), t % Q, Q));
+    else
+      xd[idx] = xdesc(tf.ph, xnf(tb, tf, l - 1, d.ap1, t / Q, Q), xnf(tb, tf, l - 1, d.ap2, t % Q, Q));
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 10 * Q2; idx += blockDim.x) {
+    const int c2 = idx & 1, n = idx >> 1;
+    g[idx] = g_eval(tf.ph, xd[n], p2f(tb, tf, lb + 1, 2 * d.b2 + c2, Q, Q));
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 20 * Q2; idx += blockDim.x) {
+    if (idx < 16 * Q2) {
+      const int sg = idx / (4 * Q2), c = (idx / Q2) & 3, t = idx % Q2;
+      const df rho = rhof(tb, tf, lb + 1, 2 * d.b1 + (c >> 1), Q, Q);
+      ea[idx] = expi_df(df_mul(rho, g[(sg * Q2 + t) * 2 + (c & 1)]));
+    } else {
+      const int k = idx - 16 * Q2, c = k / Q2, t = k % Q2;
+      const df rho = rhof(tb, tf, lb + 1, 2 * d.b1 + (c >> 1), Q, Q);
+      eq[k] = expi_df(df_mul(rho, g[(4 * Q2 + t) * 2 + (c & 1)]));
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ float2 conjf2(float2 v) { return make_float2(v.x, -v.y); }
+
+// ---------------------------------------------------------------------------
+// FP32 translation, type P (see k_trans_p): out_j = post_j (.) sum_i (T^{i1} (x) T^{i2}) (pre_{j,i} (.) in_i)
+// FWD: recursion in p (eq. alg2b); !FWD: conjugate transpose of the recursion in x.
+// blockDim = 32 Q.  Shared memory: phases 20 Q^2, input/output subtile 4 Q^2 kRS,
+// intermediate 8 Q^2 kRS (float2).
+// ---------------------------------------------------------------------------
+template <int Q, bool FWD>
+__global__ void __launch_bounds__(32 * Q) k32_trans_p(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm,
+                                                       const float2 *__restrict__ in, float2 *__restrict__ out) {
+  constexpr int Q2 = Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *pre_s = (float2 *)smem_raw;       // [4 j][4 i][Q2]
+  float2 *post_s = pre_s + 16 * Q2;         // [4 j][Q2]
+  float2 *io_s = post_s + 4 * Q2;           // [4][kRS][Q2]
+  float2 *z_s = io_s + 4 * kRS * Q2;        // [4 j][2 i1][kRS][Q2]
+  const int l = g.l, lb = g.L - g.l, e = g.e;
+  const long long unit = blockIdx.x;
+  const UnitIdx d = unit_decode(unit, l, lb, e);
+  const int r0 = blockIdx.y * kRMax;
+  const int rc = min(kRMax, g.nrhs - r0);
+  const long long nrq = (long long)g.nrhs * Q2;
+
+  // phase factors of the unit, shared by all right-hand sides
+  if (FWD) {
+    // pre[j=sigma][i=c] = ec[sigma][c], post[j=sigma] = conj ep[sigma]
+    family_centres<Q>(tb, tf, ph, d, l, lb, pre_s, post_s, (unsigned char *)z_s);
+    for (int idx = threadIdx.x; idx < 4 * Q2; idx += blockDim.x) post_s[idx] = conjf2(post_s[idx]);
+  } else {
+    // pre[j=c][i=sigma] = conj ea[sigma][c], post[j=c] = eq[c]
+    float2 *ea = z_s;  // the intermediate buffer holds ea until the subtile loop starts
+    family_nodes<Q>(tb, tf, ph, d, l, lb, ea, post_s, (unsigned char *)io_s);
+    for (int idx = threadIdx.x; idx < 16 * Q2; idx += blockDim.x) {
+      const int sg = idx / (4 * Q2), c = (idx / Q2) & 3, t = idx % Q2;
+      pre_s[(c * 4 + sg) * Q2 + t] = conjf2(ea[idx]);
+    }
+  }
+  __syncthreads();
+
+  for (int rs0 = 0; rs0 < rc; rs0 += kRS) {
+    const int rs = min(kRS, rc - rs0);
+    // stage the four input blocks of this subtile
+    for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
+      const int i = idx / (rs * Q2), k = idx % (rs * Q2);
+      const long long pr = FWD ? pair_child_b(d, i, lb, e) : pair_child_a(d, i, l, lb, e);
+      io_s[i * kRS * Q2 + k] = in[pr * nrq + (long long)(r0 + rs0) * Q2 + k];
+    }
+    __syncthreads();
+    // Z_{j,i1}[t'1][t2] = sum_{i2,t'2} T^{i2}[t2][t'2] (pre (.) in)_{(i1,i2)}[t'1][t'2]
+    for (int task = threadIdx.x; task < 8 * kRS * Q; task += blockDim.x) {
+      const int tp1 = task % Q, r = (task / Q) % kRS, i1 = (task / (Q * kRS)) & 1, j = task / (2 * Q * kRS);
+      if (r >= rs) continue;
+      float2 s[2][Q];
+#pragma unroll
+      for (int i2 = 0; i2 < 2; i2++)
+#pragma unroll
+        for (int tp2 = 0; tp2 < Q; tp2++) {
+          const int i = i1 * 2 + i2;
+          s[i2][tp2] = cmul(pre_s[(j * 4 + i) * Q2 + tp1 * Q + tp2], io_s[(i * kRS + r) * Q2 + tp1 * Q + tp2]);
+        }
+      float2 *zrow = z_s + ((j * 2 + i1) * kRS + r) * Q2 + tp1 * Q;
+#pragma unroll
+      for (int t2 = 0; t2 < Q; t2++) {
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int i2 = 0; i2 < 2; i2++)
+#pragma unroll
+          for (int tp2 = 0; tp2 < Q; tp2++) {
+            ax = __fmaf_rn(tm.T[i2][t2][tp2], s[i2][tp2].x, ax);
+            ay = __fmaf_rn(tm.T[i2][t2][tp2], s[i2][tp2].y, ay);
+          }
+        zrow[t2] = make_float2(ax, ay);
+      }
+    }
+    __syncthreads();
+    // Y_j[t1][t2] = sum_{i1,t'1} T^{i1}[t1][t'1] Z_{j,i1}[t'1][t2];  out_j = post_j (.) Y_j -> io_s
+    for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
+      const int t2 = task % Q, r = (task / Q) % kRS, j = task / (Q * kRS);
+      if (r >= rs) continue;
+      float2 zc[2][Q];
+#pragma unroll
+      for (int i1 = 0; i1 < 2; i1++)
+#pragma unroll
+        for (int tp1 = 0; tp1 < Q; tp1++) zc[i1][tp1] = z_s[((j * 2 + i1) * kRS + r) * Q2 + tp1 * Q + t2];
+#pragma unroll
+      for (int t1 = 0; t1 < Q; t1++) {
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int i1 = 0; i1 < 2; i1++)
+#pragma unroll
+          for (int tp1 = 0; tp1 < Q; tp1++) {
+            ax = __fmaf_rn(tm.T[i1][t1][tp1], zc[i1][tp1].x, ax);
+            ay = __fmaf_rn(tm.T[i1][t1][tp1], zc[i1][tp1].y, ay);
+          }
+        io_s[(j * kRS + r) * Q2 + t1 * Q + t2] = cmul(post_s[j * Q2 + t1 * Q + t2], make_float2(ax, ay));
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
+      const int j = idx / (rs * Q2), k = idx % (rs * Q2);
+      const long long pr = FWD ? pair_child_a(d, j, l, lb, e) : pair_child_b(d, j, lb, e);
+      out[pr * nrq + (long long)(r0 + rs0) * Q2 + k] = io_s[j * kRS * Q2 + k];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 translation, type X (see k_trans_x): out_j = sum_i post_{j,i} (.) (T^{j1} (x) T^{j2})^T (pre_i (.) in_i)
+// FWD: recursion in x (eq. alg2c); !FWD: conjugate transpose of the recursion in p.
+// ---------------------------------------------------------------------------
+template <int Q, bool FWD>
+__global__ void __launch_bounds__(32 * Q) k32_trans_x(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm,
+                                                       const float2 *__restrict__ in, float2 *__restrict__ out) {
+  constexpr int Q2 = Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *pre_s = (float2 *)smem_raw;   // [4 i][Q2]
+  float2 *post_s = pre_s + 4 * Q2;      // [4 j][4 i][Q2]
+  float2 *io_s = post_s + 16 * Q2;      // [4][kRS][Q2]
+  float2 *w_s = io_s + 4 * kRS * Q2;    // [4 i][2 j1][kRS][Q2]
+  const int l = g.l, lb = g.L - g.l, e = g.e;
+  const long long unit = blockIdx.x;
+  const UnitIdx d = unit_decode(unit, l, lb, e);
+  const int r0 = blockIdx.y * kRMax;
+  const int rc = min(kRMax, g.nrhs - r0);
+  const long long nrq = (long long)g.nrhs * Q2;
+
+  if (FWD) {
+    // pre[i=c] = conj eq[c], post[j=sigma][i=c] = ea[sigma][c]
+    family_nodes<Q>(tb, tf, ph, d, l, lb, post_s, pre_s, (unsigned char *)io_s);
+    for (int idx = threadIdx.x; idx < 4 * Q2; idx += blockDim.x) pre_s[idx] = conjf2(pre_s[idx]);
+  } else {
+    // pre[i=sigma] = ep[sigma], post[j=c][i=sigma] = conj ec[sigma][c]
+    float2 *ec = w_s;
+    family_centres<Q>(tb, tf, ph, d, l, lb, ec, pre_s, (unsigned char *)io_s);
+    for (int idx = threadIdx.x; idx < 16 * Q2; idx += blockDim.x) {
+      const int sg = idx / (4 * Q2), c = (idx / Q2) & 3, u = idx % Q2;
+      post_s[(c * 4 + sg) * Q2 + u] = conjf2(ec[idx]);
+    }
+  }
+  __syncthreads();
+
+  for (int rs0 = 0; rs0 < rc; rs0 += kRS) {
+    const int rs = min(kRS, rc - rs0);
+    for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
+      const int i = idx / (rs * Q2), k = idx % (rs * Q2);
+      const long long pr = FWD ? pair_child_b(d, i, lb, e) : pair_child_a(d, i, l, lb, e);
+      io_s[i * kRS * Q2 + k] = cmul(pre_s[i * Q2 + k % Q2], in[pr * nrq + (long long)(r0 + rs0) * Q2 + k]);
+    }
+    __syncthreads();
+    // W_{i,j1}[t1][t'2] = sum_{t'1} T^{j1}[t'1][t1] S_i[t'1][t'2]
+    for (int task = threadIdx.x; task < 8 * kRS * Q; task += blockDim.x) {
+      const int tp2 = task % Q, r = (task / Q) % kRS, j1 = (task / (Q * kRS)) & 1, i = task / (2 * Q * kRS);
+      if (r >= rs) continue;
+      float2 col[Q];
+#pragma unroll
+      for (int tp1 = 0; tp1 < Q; tp1++) col[tp1] = io_s[(i * kRS + r) * Q2 + tp1 * Q + tp2];
+      float2 *wb = w_s + ((i * 2 + j1) * kRS + r) * Q2 + tp2;
+#pragma unroll
+      for (int t1 = 0; t1 < Q; t1++) {
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int tp1 = 0; tp1 < Q; tp1++) {
+          ax = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].x, ax);
+          ay = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].y, ay);
+        }
+        wb[t1 * Q] = make_float2(ax, ay);
+      }
+    }
+    __syncthreads();
+    // out_j[t1][t2] = sum_i post_{j,i}[t1][t2] sum_{t'2} T^{j2}[t'2][t2] W_{i,j1}[t1][t'2]  -> io_s
+    for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
+      const int t1 = task % Q, r = (task / Q) % kRS, j = task / (Q * kRS);
+      if (r >= rs) continue;
+      const int j1 = j >> 1, j2 = j & 1;
+      float ax[Q], ay[Q];
+#pragma unroll
+      for (int t2 = 0; t2 < Q; t2++) ax[t2] = ay[t2] = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        float2 row[Q];
+#pragma unroll
+        for (int tp2 = 0; tp2 < Q; tp2++) row[tp2] = w_s[((i * 2 + j1) * kRS + r) * Q2 + t1 * Q + tp2];
+#pragma unroll
+        for (int t2 = 0; t2 < Q; t2++) {
+          float vx = 0.f, vy = 0.f;
+#pragma unroll
+          for (int tp2 = 0; tp2 < Q; tp2++) {
+            vx = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].x, vx);
+            vy = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].y, vy);
+          }
+          const float2 p = post_s[(j * 4 + i) * Q2 + t1 * Q + t2];
+          ax[t2] = __fmaf_rn(p.x, vx, __fmaf_rn(-p.y, vy, ax[t2]));
+          ay[t2] = __fmaf_rn(p.x, vy, __fmaf_rn(p.y, vx, ay[t2]));
+        }
+      }
+      // io_s (the premodulated inputs) was last read in the W pass, so it can take the outputs
+      float2 *dst = io_s + (j * kRS + r) * Q2 + t1 * Q;
+#pragma unroll
+      for (int t2 = 0; t2 < Q; t2++) dst[t2] = make_float2(ax[t2], ay[t2]);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
+      const int j = idx / (rs * Q2), k = idx % (rs * Q2);
+      const long long pr = FWD ? pair_child_a(d, j, l, lb, e) : pair_child_b(d, j, lb, e);
+      out[pr * nrq + (long long)(r0 + rs0) * Q2 + k] = io_s[j * kRS * Q2 + k];
+    }
+    __syncthreads();
+  }
+}
+
+// e^{2 pi i theta(x, p)} for the FP32 form: x by its two 1D node entries (FP64 and df
+// copies), p by its polar node entries.  Homogeneous phases go through df
+// arithmetic; the separable test phase through FP64.
+__device__ __forceinline__ float2 e32(const Phase &ph, const TablesF &tf, const XNode &x1, const XNode &x2,
+                                      const XNodeF &f1, const XNodeF &f2, const P1Node &u, const P2Node &v,
+                                      const df &rho, const P2NodeF &vf) {
+  if (ph.id == 3) return expi<float>(theta_xp(ph, x1, x2, u, v));
+  return expi_df(df_mul(rho, g_eval(tf.ph, xdesc(tf.ph, f1, f2), vf)));
+}
+// e^{2 pi i Phi(x, k)} at a lattice source.
+__device__ __forceinline__ float2 e32k(const Phase &ph, const TablesF &tf, const XNode &x1, const XNode &x2,
+                                       const XNodeF &f1, const XNodeF &f2, const Src &k, const SrcF &kf) {
+  if (ph.id == 3) return expi<float>(theta_xk(ph, x1, x2, k));
+  return expi_df(theta_k(tf.ph, xdesc(tf.ph, f1, f2), kf.k1, kf.k2));
+}
+
+// ---------------------------------------------------------------------------
+// FP32 switch (eq. alg2m): one CTA per pair (A, B) at level lm and up to 32 RHS.
+//   FWD : out[t] = sum_s e(x^A_t, p^B_s) in[s];   !FWD: out[s] = sum_t conj e(x^A_t, p^B_s) in[t].
+// theta(x_t, p_s) = rho(s1) G(x_t, p2_{s2}): q^3 evaluations of G, q^4 products.
+// Contraction: each thread owns 3 output rows x 4 RHS.
+// ---------------------------------------------------------------------------
+constexpr int kSwOB = 3, kSwRB = 4;
+template <int Q, bool FWD>
+__global__ void __launch_bounds__(256) k32_switch(Tables tb, TablesF tf, Phase ph, Geom g, const float2 *__restrict__ in,
+                                                   float2 *__restrict__ out) {
+  constexpr int Q2 = Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *k_s = (float2 *)smem_raw;        // [Q2 out][Q2 in]
+  float2 *in_s = k_s + Q2 * Q2;            // [kRMax][Q2]
+  float2 *out_s = in_s + kRMax * Q2;       // [kRMax][Q2]
+  XDesc *xd = (XDesc *)out_s;              // [Q2]      (before the contraction)
+  df *gt = (df *)(xd + Q2);                // [Q2][Q]
+  const int l = g.l, lb = g.L - g.l, e = g.e;
+  const long long pr = blockIdx.x;
+  const int nb2 = 1 << (lb + e);
+  const long long nBl = (1LL << lb) * nb2;
+  const long long a = pr / nBl, b = pr - a * nBl;
+  const int a1 = (int)(a >> l), a2 = (int)(a & ((1LL << l) - 1));
+  const int b1 = (int)(b / nb2), b2 = (int)(b - (long long)b1 * nb2);
+  const int r0 = blockIdx.y * kRMax;
+  const int rc = min(kRMax, g.nrhs - r0);
+  const long long nrq = (long long)g.nrhs * Q2;
+
+  for (int idx = threadIdx.x; idx < rc * Q2; idx += blockDim.x) in_s[idx] = in[pr * nrq + (long long)r0 * Q2 + idx];
+  if (ph.id == 3) {
+    for (int idx = threadIdx.x; idx < Q2 * Q2; idx += blockDim.x) {
+      const int o = idx / Q2, i = idx % Q2;
+      const int t = FWD ? o : i, s = FWD ? i : o;
+      float2 v = expi<float>(theta_xp(ph, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q), pn1(tb, lb, b1, s / Q, Q),
+                                      pn2(tb, lb, b2, s % Q, Q)));
+      k_s[idx] = FWD ? v : conjf2(v);
+    }
+  } else {
+    for (int t = threadIdx.x; t < Q2; t += blockDim.x)
+      xd[t] = xdesc(tf.ph, xnf(tb, tf, l, a1, t / Q, Q), xnf(tb, tf, l, a2, t % Q, Q));
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Q2 * Q; idx += blockDim.x)
+      gt[idx] = g_eval(tf.ph, xd[idx / Q], p2f(tb, tf, lb, b2, idx % Q, Q));
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Q2 * Q2; idx += blockDim.x) {
+      const int o = idx / Q2, i = idx % Q2;
+      const int t = FWD ? o : i, s = FWD ? i : o;
+      const float2 v = expi_df(df_mul(rhof(tb, tf, lb, b1, s / Q, Q), gt[t * Q + s % Q]));
+      k_s[idx] = FWD ? v : conjf2(v);
+    }
+  }
+  __syncthreads();
+  constexpr int NOG = (Q2 + kSwOB - 1) / kSwOB;
+  const int nrg = (rc + kSwRB - 1) / kSwRB;
+  for (int task = threadIdx.x; task < NOG * nrg; task += blockDim.x) {
+    const int rg = task % nrg, og = task / nrg;
+    float ax[kSwOB][kSwRB], ay[kSwOB][kSwRB];
+#pragma unroll
+    for (int a_ = 0; a_ < kSwOB; a_++)
+#pragma unroll
+      for (int c_ = 0; c_ < kSwRB; c_++) ax[a_][c_] = ay[a_][c_] = 0.f;
+    int orow[kSwOB], rr[kSwRB];
+#pragma unroll
+    for (int a_ = 0; a_ < kSwOB; a_++) orow[a_] = min(og * kSwOB + a_, Q2 - 1);
+#pragma unroll
+    for (int c_ = 0; c_ < kSwRB; c_++) rr[c_] = min(rg * kSwRB + c_, rc - 1);
+#pragma unroll 3
+    for (int i = 0; i < Q2; i++) {
+      float2 kv[kSwOB], iv[kSwRB];
+#pragma unroll
+      for (int a_ = 0; a_ < kSwOB; a_++) kv[a_] = k_s[orow[a_] * Q2 + i];
+#pragma unroll
+      for (int c_ = 0; c_ < kSwRB; c_++) iv[c_] = in_s[rr[c_] * Q2 + i];
+#pragma unroll
+      for (int a_ = 0; a_ < kSwOB; a_++)
+#pragma unroll
+        for (int c_ = 0; c_ < kSwRB; c_++) {
+          ax[a_][c_] = __fmaf_rn(kv[a_].x, iv[c_].x, __fmaf_rn(-kv[a_].y, iv[c_].y, ax[a_][c_]));
+          ay[a_][c_] = __fmaf_rn(kv[a_].x, iv[c_].y, __fmaf_rn(kv[a_].y, iv[c_].x, ay[a_][c_]));
+        }
+    }
+#pragma unroll
+    for (int a_ = 0; a_ < kSwOB; a_++)
+#pragma unroll
+      for (int c_ = 0; c_ < kSwRB; c_++) {
+        const int o = og * kSwOB + a_, r = rg * kSwRB + c_;
+        if (o < Q2 && r < rc) out_s[r * Q2 + o] = make_float2(ax[a_][c_], ay[a_][c_]);
+      }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < rc * Q2; idx += blockDim.x) out[pr * nrq + (long long)r0 * Q2 + idx] = out_s[idx];
+}
+
+// ---------------------------------------------------------------------------
+// FP32 initialization (eq. alg2a), as k_init with df phases; one CTA per box B,
+// up to 32 RHS, GA boxes A at a time.
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(256) k32_init(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc, int GA,
+                                                 const float2 *__restrict__ f, float2 *__restrict__ st) {
+  constexpr int Q2 = Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l0 = g.l, lb = g.L - g.l, e = g.e;
+  const int box = blockIdx.x;
+  const int nb2 = 1 << (lb + e);
+  const int b1 = box / nb2, b2 = box % nb2;
+  const int r0 = blockIdx.y * kRMax;
+  const int rt = min(kRMax, g.nrhs - r0);
+  const int j0 = tb.box_off[box], ns = tb.box_off[box + 1] - j0;
+  const long long NN = 1LL << (2 * g.L);
+  float2 *fv = (float2 *)smem_raw;     // [maxsrc][kRMax]
+  float2 *pk = fv + maxsrc * kRMax;    // [GA][maxsrc]
+  float2 *post = pk + GA * maxsrc;     // [GA][Q2]
+  float *w = (float *)(post + GA * Q2);  // [maxsrc][2Q]
+  for (int idx = threadIdx.x; idx < ns * rt; idx += blockDim.x) {
+    const int j = idx / rt, r = idx % rt;
+    fv[j * kRMax + r] = f[(long long)(r0 + r) * NN + tb.src_f[j0 + j]];
+  }
+  for (int idx = threadIdx.x; idx < ns * 2 * Q; idx += blockDim.x) w[idx] = (float)tb.src_w[(long long)j0 * 2 * Q + idx];
+  const int nA1 = 1 << l0, nA = nA1 * nA1;
+  const long long nB = (1LL << lb) * nb2;
+  const long long nrq = (long long)g.nrhs * Q2;
+  for (int A0 = 0; A0 < nA; A0 += GA) {
+    const int ga_n = min(GA, nA - A0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ga_n * (ns + Q2); idx += blockDim.x) {
+      const int ga = idx / (ns + Q2), k = idx % (ns + Q2);
+      const int A = A0 + ga, a1 = A >> l0, a2 = A & (nA1 - 1);
+      const XNode &x1 = xn(tb, l0, a1, Q, Q), &x2 = xn(tb, l0, a2, Q, Q);
+      const XNodeF &f1 = xnf(tb, tf, l0, a1, Q, Q), &f2 = xnf(tb, tf, l0, a2, Q, Q);
+      if (k < ns) {
+        pk[ga * maxsrc + k] = e32k(ph, tf, x1, x2, f1, f2, tb.src[j0 + k], tf.src[j0 + k]);
+      } else {
+        const int t = k - ns;
+        post[ga * Q2 + t] = conjf2(e32(ph, tf, x1, x2, f1, f2, pn1(tb, lb, b1, t / Q, Q), pn2(tb, lb, b2, t % Q, Q),
+                                       rhof(tb, tf, lb, b1, t / Q, Q), p2f(tb, tf, lb, b2, t % Q, Q)));
+      }
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < ga_n * rt * Q; task += blockDim.x) {
+      const int t1 = task % Q, r = (task / Q) % rt, ga = task / (Q * rt);
+      float ax[Q], ay[Q];
+#pragma unroll
+      for (int t2 = 0; t2 < Q; t2++) ax[t2] = ay[t2] = 0.f;
+      for (int j = 0; j < ns; j++) {
+        const float2 v = cmul(pk[ga * maxsrc + j], fv[j * kRMax + r]);
+        const float w1 = w[j * 2 * Q + t1];
+        const float vx = w1 * v.x, vy = w1 * v.y;
+#pragma unroll
+        for (int t2 = 0; t2 < Q; t2++) {
+          const float w2 = w[j * 2 * Q + Q + t2];
+          ax[t2] = __fmaf_rn(w2, vx, ax[t2]);
+          ay[t2] = __fmaf_rn(w2, vy, ay[t2]);
+        }
+      }
+      const int A = A0 + ga;
+      float2 *dst = st + ((long long)A * nB + box) * nrq + (long long)(r0 + r) * Q2 + t1 * Q;
+#pragma unroll
+      for (int t2 = 0; t2 < Q; t2++) dst[t2] = cmul(post[ga * Q2 + t1 * Q + t2], make_float2(ax[t2], ay[t2]));
+    }
+  }
+}
+
+// FP32 conjugate transpose of the initialization (see k_init_adj).
+template <int Q>
+__global__ void __launch_bounds__(256) k32_init_adj(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc,
+                                                     const float2 *__restrict__ st, float2 *__restrict__ fbar) {
+  constexpr int Q2 = Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l0 = g.l, lb = g.L - g.l, e = g.e;
+  const int box = blockIdx.x;
+  const int nb2 = 1 << (lb + e);
+  const int b1 = box / nb2, b2 = box % nb2;
+  const int r0 = blockIdx.y * kRMax;
+  const int rt = min(kRMax, g.nrhs - r0);
+  const int j0 = tb.box_off[box], ns = tb.box_off[box + 1] - j0;
+  const long long NN = 1LL << (2 * g.L);
+  float2 *acc = (float2 *)smem_raw;   // [maxsrc][kRMax]
+  float2 *pk = acc + maxsrc * kRMax;  // [maxsrc]
+  float2 *pt = pk + maxsrc;           // [Q2]
+  float2 *v = pt + Q2;                // [kRMax][Q2]
+  float *w = (float *)(v + kRMax * Q2);  // [maxsrc][2Q]
+  for (int idx = threadIdx.x; idx < ns * rt; idx += blockDim.x) acc[(idx / rt) * kRMax + idx % rt] = make_float2(0.f, 0.f);
+  for (int idx = threadIdx.x; idx < ns * 2 * Q; idx += blockDim.x) w[idx] = (float)tb.src_w[(long long)j0 * 2 * Q + idx];
+  const int nA1 = 1 << l0, nA = nA1 * nA1;
+  const long long nB = (1LL << lb) * nb2;
+  const long long nrq = (long long)g.nrhs * Q2;
+  for (int A = 0; A < nA; A++) {
+    const int a1 = A >> l0, a2 = A & (nA1 - 1);
+    const XNode &x1 = xn(tb, l0, a1, Q, Q), &x2 = xn(tb, l0, a2, Q, Q);
+    const XNodeF &f1 = xnf(tb, tf, l0, a1, Q, Q), &f2 = xnf(tb, tf, l0, a2, Q, Q);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ns + Q2; idx += blockDim.x) {
+      if (idx < ns) {
+        pk[idx] = conjf2(e32k(ph, tf, x1, x2, f1, f2, tb.src[j0 + idx], tf.src[j0 + idx]));
+      } else {
+        const int t = idx - ns;
+        pt[t] = e32(ph, tf, x1, x2, f1, f2, pn1(tb, lb, b1, t / Q, Q), pn2(tb, lb, b2, t % Q, Q),
+                    rhof(tb, tf, lb, b1, t / Q, Q), p2f(tb, tf, lb, b2, t % Q, Q));
+      }
+    }
+    __syncthreads();
+    const float2 *src = st + ((long long)A * nB + box) * nrq + (long long)r0 * Q2;
+    for (int idx = threadIdx.x; idx < rt * Q2; idx += blockDim.x) v[idx] = cmul(pt[idx % Q2], src[idx]);
+    __syncthreads();
+    for (int task = threadIdx.x; task < ns * rt; task += blockDim.x) {
+      const int j = task / rt, r = task % rt;
+      const float *w1 = w + j * 2 * Q, *w2 = w1 + Q;
+      float px = 0.f, py = 0.f;
+#pragma unroll
+      for (int t1 = 0; t1 < Q; t1++) {
+        float qx = 0.f, qy = 0.f;
+#pragma unroll
+        for (int t2 = 0; t2 < Q; t2++) {
+          const float2 vv = v[r * Q2 + t1 * Q + t2];
+          qx = __fmaf_rn(w2[t2], vv.x, qx);
+          qy = __fmaf_rn(w2[t2], vv.y, qy);
+        }
+        px = __fmaf_rn(w1[t1], qx, px);
+        py = __fmaf_rn(w1[t1], qy, py);
+      }
+      const float2 p = cmul(pk[j], make_float2(px, py));
+      float2 a_ = acc[j * kRMax + r];
+      acc[j * kRMax + r] = make_float2(a_.x + p.x, a_.y + p.y);
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < ns * rt; idx += blockDim.x) {
+    const int j = idx / rt, r = idx % rt;
+    fbar[(long long)(r0 + r) * NN + tb.src_f[j0 + j]] = acc[j * kRMax + r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 termination (eq. alg2d), as k_term with df phases; one CTA per box A,
+// up to 32 RHS, the boxes B summed in a fixed order.
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(256) k32_term(Tables tb, TablesF tf, Phase ph, Geom g, VMat<float, Q> vm,
+                                                 const float2 *__restrict__ st, float2 *__restrict__ u) {
+  constexpr int Q2 = Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l = g.l, lb = g.L - g.l, e = g.e;
+  const int M = 1 << g.s, M2 = M * M;
+  const int A = blockIdx.x, nA1 = 1 << l;
+  const int a1 = A >> l, a2 = A & (nA1 - 1);
+  const int r0 = blockIdx.y * kRMax;
+  const int rt = min(kRMax, g.nrhs - r0);
+  const int nb2 = 1 << (lb + e);
+  const int nB = (1 << lb) * nb2;
+  const long long NN = 1LL << (2 * g.L);
+  float2 *acc = (float2 *)smem_raw;  // [rt][M2]
+  float2 *pre = acc + kRMax * M2;    // [Q2]
+  float2 *post = pre + Q2;           // [M2]
+  float2 *sv = post + M2;            // [rt][Q2]
+  float2 *y = sv + kRMax * Q2;       // [rt][M][Q]
+  for (int idx = threadIdx.x; idx < rt * M2; idx += blockDim.x) acc[idx] = make_float2(0.f, 0.f);
+  const long long nrq = (long long)g.nrhs * Q2;
+  for (int B = 0; B < nB; B++) {
+    const int b1 = B / nb2, b2 = B % nb2;
+    const P1Node &c1 = pn1(tb, lb, b1, Q, Q);
+    const P2Node &c2 = pn2(tb, lb, b2, Q, Q);
+    const df rho = rhof(tb, tf, lb, b1, Q, Q);
+    const P2NodeF &c2f = p2f(tb, tf, lb, b2, Q, Q);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
+      if (idx < Q2) {
+        pre[idx] = conjf2(e32(ph, tf, xn(tb, l, a1, idx / Q, Q), xn(tb, l, a2, idx % Q, Q), xnf(tb, tf, l, a1, idx / Q, Q),
+                              xnf(tb, tf, l, a2, idx % Q, Q), c1, c2, rho, c2f));
+      } else {
+        const int m = idx - Q2, i1 = a1 * M + m / M, i2 = a2 * M + m % M;
+        post[m] = e32(ph, tf, tb.xgrid[i1], tb.xgrid[i2], tf.xgrid[i1], tf.xgrid[i2], c1, c2, rho, c2f);
+      }
+    }
+    __syncthreads();
+    const float2 *src = st + ((long long)A * nB + B) * nrq + (long long)r0 * Q2;
+    for (int idx = threadIdx.x; idx < rt * Q2; idx += blockDim.x) sv[idx] = cmul(pre[idx % Q2], src[idx]);
+    __syncthreads();
+    for (int task = threadIdx.x; task < rt * M * Q; task += blockDim.x) {
+      const int t2 = task % Q, m1 = (task / Q) % M, r = task / (Q * M);
+      float ax = 0.f, ay = 0.f;
+#pragma unroll
+      for (int t1 = 0; t1 < Q; t1++) {
+        const float2 s = sv[r * Q2 + t1 * Q + t2];
+        ax = __fmaf_rn(vm.V[m1][t1], s.x, ax);
+        ay = __fmaf_rn(vm.V[m1][t1], s.y, ay);
+      }
+      y[(r * M + m1) * Q + t2] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < rt * M2; task += blockDim.x) {
+      const int m = task % M2, r = task / M2, m1 = m / M, m2 = m % M;
+      float ax = 0.f, ay = 0.f;
+#pragma unroll
+      for (int t2 = 0; t2 < Q; t2++) {
+        const float2 s = y[(r * M + m1) * Q + t2];
+        ax = __fmaf_rn(vm.V[m2][t2], s.x, ax);
+        ay = __fmaf_rn(vm.V[m2][t2], s.y, ay);
+      }
+      const float2 p = cmul(post[m], make_float2(ax, ay));
+      const float2 a_ = acc[task];
+      acc[task] = make_float2(a_.x + p.x, a_.y + p.y);
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < rt * M2; idx += blockDim.x) {
+    const int m = idx % M2, r = idx / M2;
+    const long long i1 = (long long)a1 * M + m / M, i2 = (long long)a2 * M + m % M;
+    u[(long long)(r0 + r) * NN + (i1 << g.L) + i2] = acc[idx];
+  }
+}
+
+// FP32 conjugate transpose of the termination (see k_term_adj).
+template <int Q>
+__global__ void __launch_bounds__(256) k32_term_adj(Tables tb, TablesF tf, Phase ph, Geom g, VMat<float, Q> vm,
+                                                     const float2 *__restrict__ gin, float2 *__restrict__ st) {
+  constexpr int Q2 = Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l = g.l, lb = g.L - g.l, e = g.e;
+  const int M = 1 << g.s, M2 = M * M;
+  const int A = blockIdx.x, nA1 = 1 << l;
+  const int a1 = A >> l, a2 = A & (nA1 - 1);
+  const int r0 = blockIdx.y * kRMax;
+  const int rt = min(kRMax, g.nrhs - r0);
+  const int nb2 = 1 << (lb + e);
+  const int nB = (1 << lb) * nb2;
+  const long long NN = 1LL << (2 * g.L);
+  float2 *gv = (float2 *)smem_raw;  // [rt][M2]
+  float2 *pre = gv + kRMax * M2;    // [M2]
+  float2 *post = pre + M2;          // [Q2]
+  float2 *gm = post + Q2;           // [rt][M2]
+  float2 *y = gm + kRMax * M2;      // [rt][Q][M]
+  for (int idx = threadIdx.x; idx < rt * M2; idx += blockDim.x) {
+    const int m = idx % M2, r = idx / M2;
+    const long long i1 = (long long)a1 * M + m / M, i2 = (long long)a2 * M + m % M;
+    gv[idx] = gin[(long long)(r0 + r) * NN + (i1 << g.L) + i2];
+  }
+  const long long nrq = (long long)g.nrhs * Q2;
+  for (int B = 0; B < nB; B++) {
+    const int b1 = B / nb2, b2 = B % nb2;
+    const P1Node &c1 = pn1(tb, lb, b1, Q, Q);
+    const P2Node &c2 = pn2(tb, lb, b2, Q, Q);
+    const df rho = rhof(tb, tf, lb, b1, Q, Q);
+    const P2NodeF &c2f = p2f(tb, tf, lb, b2, Q, Q);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
+      if (idx < M2) {
+        const int i1 = a1 * M + idx / M, i2 = a2 * M + idx % M;
+        pre[idx] = conjf2(e32(ph, tf, tb.xgrid[i1], tb.xgrid[i2], tf.xgrid[i1], tf.xgrid[i2], c1, c2, rho, c2f));
+      } else {
+        const int t = idx - M2;
+        post[t] = e32(ph, tf, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q), xnf(tb, tf, l, a1, t / Q, Q),
+                      xnf(tb, tf, l, a2, t % Q, Q), c1, c2, rho, c2f);
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < rt * M2; idx += blockDim.x) gm[idx] = cmul(pre[idx % M2], gv[idx]);
+    __syncthreads();
+    for (int task = threadIdx.x; task < rt * Q * M; task += blockDim.x) {
+      const int m2 = task % M, t1 = (task / M) % Q, r = task / (M * Q);
+      float ax = 0.f, ay = 0.f;
+      for (int m1 = 0; m1 < M; m1++) {
+        const float2 s = gm[r * M2 + m1 * M + m2];
+        ax = __fmaf_rn(vm.V[m1][t1], s.x, ax);
+        ay = __fmaf_rn(vm.V[m1][t1], s.y, ay);
+      }
+      y[(r * Q + t1) * M + m2] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    float2 *dst = st + ((long long)A * nB + B) * nrq + (long long)r0 * Q2;
+    for (int task = threadIdx.x; task < rt * Q2; task += blockDim.x) {
+      const int t = task % Q2, r = task / Q2, t1 = t / Q, t2 = t % Q;
+      float ax = 0.f, ay = 0.f;
+      for (int m2 = 0; m2 < M; m2++) {
+        const float2 s = y[(r * Q + t1) * M + m2];
+        ax = __fmaf_rn(vm.V[m2][t2], s.x, ax);
+        ay = __fmaf_rn(vm.V[m2][t2], s.y, ay);
+      }
+      dst[task] = cmul(post[t], make_float2(ax, ay));
+    }
+  }
+}
+
+}  // namespace fio

@@ -39,7 +39,7 @@ using namespace fio;
 constexpr size_t kScratchBytes = (size_t)8 << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxN = 32, kMaxQ = 9, kMaxE = 2, kMaxDevices = 64;
+constexpr int kMaxN = 32, kMaxE = 2, kMaxDevices = 64;
 constexpr int kMaxNN = kMaxN * kMaxN;
 constexpr int kMaxBoxes = kMaxN * (kMaxN << kMaxE);                    // T_P boxes at level L-s
 

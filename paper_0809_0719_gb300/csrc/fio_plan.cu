@@ -289,12 +289,29 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   d.maxsrc = maxsrc;
   d.nbox_init = (int)nbox;
 
+  // df copies of the tables for the FP32 form (phases on the FMA pipe)
+  const bool f32 = precision == FIO_F32;
+  std::vector<XNodeF> xnodeF, xgridF;
+  std::vector<P1NodeF> p1nodeF;
+  std::vector<P2NodeF> p2nodeF;
+  std::vector<SrcF> srcF;
+  if (f32) {
+    for (const XNode &n : xnode) xnodeF.push_back({df_split(n.x), df_split(n.s), df_split(n.c)});
+    for (const XNode &n : xgrid) xgridF.push_back({df_split(n.x), df_split(n.s), df_split(n.c)});
+    for (const P1Node &n : p1node) p1nodeF.push_back({df_split(n.rho)});
+    for (const P2Node &n : p2node) p2nodeF.push_back({df_split(n.c), df_split(n.s)});
+    for (const Src &k : src) srcF.push_back({(float)k.k1, (float)k.k2});
+  }
+
   // ---- device: one table allocation, two state buffers
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t b_x = al(xnode.size() * sizeof(XNode)), b_p1 = al(p1node.size() * sizeof(P1Node)),
                b_p2 = al(p2node.size() * sizeof(P2Node)), b_g = al(N * sizeof(XNode)), b_s = al(NN * sizeof(Src)),
                b_f = al(NN * sizeof(int)), b_w = al(srcw.size() * sizeof(double)), b_o = al((nbox + 1) * sizeof(int));
-  const size_t tbytes = b_x + b_p1 + b_p2 + b_g + b_s + b_f + b_w + b_o;
+  const size_t b_xF = al(xnodeF.size() * sizeof(XNodeF)), b_gF = al(xgridF.size() * sizeof(XNodeF)),
+               b_p1F = al(p1nodeF.size() * sizeof(P1NodeF)), b_p2F = al(p2nodeF.size() * sizeof(P2NodeF)),
+               b_sF = al(srcF.size() * sizeof(SrcF));
+  const size_t tbytes = b_x + b_p1 + b_p2 + b_g + b_s + b_f + b_w + b_o + b_xF + b_gF + b_p1F + b_p2F + b_sF;
   const size_t sbytes = (((size_t)NN * q * q) << e) * (size_t)nrhs_max * (precision == FIO_F64 ? 16 : 8);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
@@ -325,6 +342,19 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   d.tb.src_f = (const int *)up(srcf.data(), NN * sizeof(int), b_f);
   d.tb.src_w = (const double *)up(srcw.data(), srcw.size() * sizeof(double), b_w);
   d.tb.box_off = (const int *)up(cnt.data(), (nbox + 1) * sizeof(int), b_o);
+  d.tf = TablesF();
+  if (f32) {
+    d.tf.xnode = (const XNodeF *)up(xnodeF.data(), xnodeF.size() * sizeof(XNodeF), b_xF);
+    d.tf.xgrid = (const XNodeF *)up(xgridF.data(), xgridF.size() * sizeof(XNodeF), b_gF);
+    d.tf.p1node = (const P1NodeF *)up(p1nodeF.data(), p1nodeF.size() * sizeof(P1NodeF), b_p1F);
+    d.tf.p2node = (const P2NodeF *)up(p2nodeF.data(), p2nodeF.size() * sizeof(P2NodeF), b_p2F);
+    d.tf.src = (const SrcF *)up(srcF.data(), srcF.size() * sizeof(SrcF), b_sF);
+    d.tf.ph.id = phase_id;
+    d.tf.ph.a = df_split(d.ph.a);
+    d.tf.ph.m = df_split(d.ph.m);
+    d.tf.ph.ib = df_split(d.ph.ib);
+    d.tf.ph.lam = df_split(d.ph.lam);
+  }
   if ((ce = cudaGetLastError()) != cudaSuccess) {
     cudaFree(tb);
     delete p;

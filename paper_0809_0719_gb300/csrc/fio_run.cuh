@@ -3,7 +3,7 @@
 #pragma once
 #include <algorithm>
 
-#include "fio_kernels.cuh"
+#include "fio_k32.cuh"
 
 namespace fio {
 
@@ -29,6 +29,7 @@ struct Prof {
 // Everything a run needs from a plan (plain data, no ownership).
 struct PlanDev {
   Tables tb;
+  TablesF tf;  // df tables of FIO_F32 plans; tf.xnode == NULL selects the generic kernels
   Phase ph;
   int N, L, q, s, e, l0, lm, l1, precision, nrhs_max, maxsrc, nbox_init;
   void *state[2];
@@ -102,8 +103,30 @@ template <typename R, int Q> struct Runner {
     return err == cudaSuccess ? 0 : (int)err;
   }
 
+  bool fast32() const { return sizeof(R) == 4 && p.tf.xnode != nullptr; }
+
   // Translation at level l (forward: l-1 -> l; adjoint: l -> l-1).
   template <bool TYPE_P, bool FWD> int trans(int l, const CT *in, CT *out) {
+    if constexpr (sizeof(R) == 4) {
+      if (fast32()) {
+        const long long nunits = (1LL << (2 * (l - 1))) * nb_at(p.L - l);
+        const Geom g = geom(l, kRMax, 1, nunits);
+        dim3 grid((unsigned)nunits, (unsigned)((nrhs + kRMax - 1) / kRMax));
+        const int smem = (20 + 12 * kRS) * Q2 * (int)sizeof(float2);
+        if (count_only) return check();
+        pre(TYPE_P ? (FWD ? K_TRANS_P : K_TRANS_P_ADJ) : (FWD ? K_TRANS_X : K_TRANS_X_ADJ));
+        if (TYPE_P) {
+          auto k = k32_trans_p<Q, FWD>;
+          set_smem(k, p.smem_optin);
+          k<<<grid, 32 * Q, smem, st>>>(p.tb, p.tf, p.ph, g, tmat(), (const float2 *)in, (float2 *)out);
+        } else {
+          auto k = k32_trans_x<Q, FWD>;
+          set_smem(k, p.smem_optin);
+          k<<<grid, 32 * Q, smem, st>>>(p.tb, p.tf, p.ph, g, tmat(), (const float2 *)in, (float2 *)out);
+        }
+        return check();
+      }
+    }
     const int rt = std::min(nrhs, sizeof(R) == 4 ? 8 : 4);
     const int per_unit = (12 * rt * Q2 + 20 * Q2) * (int)sizeof(CT);
     int U = std::max(1, (64 + rt * Q - 1) / (rt * Q));
@@ -127,6 +150,20 @@ template <typename R, int Q> struct Runner {
   }
 
   template <bool FWD> int sw(const CT *in, CT *out) {
+    if constexpr (sizeof(R) == 4) {
+      const int smem32 = (Q2 * Q2 + 2 * kRMax * Q2) * (int)sizeof(float2);
+      if (fast32() && smem32 <= p.smem_optin) {
+        const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
+        const Geom g = geom(p.lm, kRMax, 1, pairs);
+        dim3 grid((unsigned)pairs, (unsigned)((nrhs + kRMax - 1) / kRMax));
+        if (count_only) return check();
+        pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
+        auto k = k32_switch<Q, FWD>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, 256, smem32, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out);
+        return check();
+      }
+    }
     const int rt = std::min(nrhs, 32);
     const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
     int U = 1;
@@ -146,6 +183,24 @@ template <typename R, int Q> struct Runner {
 
   int init(const CT *f, CT *out) {
     const int ms = std::max(1, p.maxsrc);
+    if constexpr (sizeof(R) == 4) {
+      if (fast32()) {
+        const int rt = std::min(nrhs, kRMax);
+        int GA = std::max(1, kThreads / (rt * Q));
+        auto bytes = [&](int ga) { return (ms * kRMax + ga * ms + ga * Q2) * 8 + ms * 2 * Q * 4; };
+        while (bytes(GA) > p.smem_optin && GA > 1) GA--;
+        if (bytes(GA) <= p.smem_optin) {
+          const Geom g = geom(p.l0, kRMax, 1, p.nbox_init);
+          dim3 grid((unsigned)p.nbox_init, (unsigned)((nrhs + kRMax - 1) / kRMax));
+          if (count_only) return check();
+          pre(K_INIT);
+          auto k = k32_init<Q>;
+          set_smem(k, p.smem_optin);
+          k<<<grid, 256, bytes(GA), st>>>(p.tb, p.tf, p.ph, g, ms, GA, (const float2 *)f, (float2 *)out);
+          return check();
+        }
+      }
+    }
     int rt = std::min(nrhs, sizeof(R) == 4 ? 32 : 8);
     int GA = std::max(1, kThreads / (rt * Q));
     auto bytes = [&](int rt_, int ga) {
@@ -166,6 +221,19 @@ template <typename R, int Q> struct Runner {
 
   int init_adj(const CT *in, CT *fbar) {
     const int ms = std::max(1, p.maxsrc);
+    if constexpr (sizeof(R) == 4) {
+      const int b32 = (ms * kRMax + ms + Q2 + kRMax * Q2) * 8 + ms * 2 * Q * 4;
+      if (fast32() && b32 <= p.smem_optin) {
+        const Geom g = geom(p.l0, kRMax, 1, p.nbox_init);
+        dim3 grid((unsigned)p.nbox_init, (unsigned)((nrhs + kRMax - 1) / kRMax));
+        if (count_only) return check();
+        pre(K_INIT_ADJ);
+        auto k = k32_init_adj<Q>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, 256, b32, st>>>(p.tb, p.tf, p.ph, g, ms, (const float2 *)in, (float2 *)fbar);
+        return check();
+      }
+    }
     int rt = std::min(nrhs, sizeof(R) == 4 ? 32 : 8);
     auto bytes = [&](int rt_) {
       return (ms * rt_ + ms + Q2 + rt_ * Q2) * (int)sizeof(CT) + ms * 2 * Q * (int)sizeof(R);
@@ -184,6 +252,20 @@ template <typename R, int Q> struct Runner {
 
   int term(const CT *in, CT *u) {
     const int M = 1 << p.s, M2 = M * M;
+    if constexpr (sizeof(R) == 4) {
+      const int b32 = (kRMax * M2 + Q2 + M2 + kRMax * Q2 + kRMax * M * Q) * 8;
+      if (fast32() && b32 <= p.smem_optin) {
+        const long long nA = 1LL << (2 * p.l1);
+        const Geom g = geom(p.l1, kRMax, 1, nA);
+        dim3 grid((unsigned)nA, (unsigned)((nrhs + kRMax - 1) / kRMax));
+        if (count_only) return check();
+        pre(K_TERM);
+        auto k = k32_term<Q>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, 256, b32, st>>>(p.tb, p.tf, p.ph, g, vmat(), (const float2 *)in, (float2 *)u);
+        return check();
+      }
+    }
     int rt = std::min(nrhs, sizeof(R) == 4 ? 32 : 8);
     auto bytes = [&](int rt_) { return (rt_ * M2 + Q2 + M2 + rt_ * Q2 + rt_ * M * Q) * (int)sizeof(CT); };
     while (bytes(rt) > p.smem_optin && rt > 1) rt--;
@@ -201,6 +283,20 @@ template <typename R, int Q> struct Runner {
 
   int term_adj(const CT *g_in, CT *out) {
     const int M = 1 << p.s, M2 = M * M;
+    if constexpr (sizeof(R) == 4) {
+      const int b32 = (2 * kRMax * M2 + M2 + Q2 + kRMax * Q * M) * 8;
+      if (fast32() && b32 <= p.smem_optin) {
+        const long long nA = 1LL << (2 * p.l1);
+        const Geom g = geom(p.l1, kRMax, 1, nA);
+        dim3 grid((unsigned)nA, (unsigned)((nrhs + kRMax - 1) / kRMax));
+        if (count_only) return check();
+        pre(K_TERM_ADJ);
+        auto k = k32_term_adj<Q>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, 256, b32, st>>>(p.tb, p.tf, p.ph, g, vmat(), (const float2 *)g_in, (float2 *)out);
+        return check();
+      }
+    }
     int rt = std::min(nrhs, sizeof(R) == 4 ? 32 : 8);
     auto bytes = [&](int rt_) { return (2 * rt_ * M2 + M2 + Q2 + rt_ * Q * M) * (int)sizeof(CT); };
     while (bytes(rt) > p.smem_optin && rt > 1) rt--;
