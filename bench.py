@@ -325,14 +325,14 @@ def run_ours(args, rank, world, dist):
 
 
 def run_small(args):
-    """--case small: only the timed applies of an N=256, q=9, 8-RHS FP32 plan (a few GB),
+    """--case small: only the timed applies of an N=256, q=9, 16-RHS FP32 plan (5.4 GB),
     forward then adjoint; the case the ncu captures use."""
     import torch
 
     from paper_0809_0719_gb300 import fio
     from paper_0809_0719_gb300.inputs import gaussian_batch
 
-    n, r = 256, 8
+    n, r = 256, 16
     plan = fio.Plan(n, Q, "ellipse", PARAMS, "f32", nrhs_max=r, s=S, e=E)
     f = torch.from_numpy(gaussian_batch(n, range(r))).to(torch.complex64).cuda()
     u = torch.empty_like(f)
@@ -350,7 +350,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="full", choices=["full", "small"],
-                    help="small: N=256 q=9 8-RHS applies only (for profiler captures)")
+                    help="small: N=256 q=9 16-RHS applies only (for profiler captures)")
     args = ap.parse_args()
     if args.case == "small":
         run_small(args)

@@ -151,213 +151,200 @@ __device__ void family_nodes(const Tables &tb, const TablesF &tf, const Phase &p
 
 __device__ __forceinline__ float2 conjf2(float2 v) { return make_float2(v.x, -v.y); }
 
+// Asynchronous 8-byte global->shared copies (LDGSTS), waited on by group.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait(int pending) {
+  if (pending) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
-// FP32 translation, type P (see k_trans_p): out_j = post_j (.) sum_i (T^{i1} (x) T^{i2}) (pre_{j,i} (.) in_i)
-// FWD: recursion in p (eq. alg2b); !FWD: conjugate transpose of the recursion in x.
-// blockDim = 32 Q.  Shared memory: phases 20 Q^2, input/output subtile 4 Q^2 kRS,
-// intermediate 8 Q^2 kRS (float2).
+// FP32 translation of both shapes (one CTA per unit, up to 32 RHS, 32 Q threads).
+// TYPE_P: out_j = post_j (.) sum_i (T^{i1} (x) T^{i2}) (pre_{j,i} (.) in_i)
+//         FWD: recursion in p (eq. alg2b); !FWD: conjugate transpose of the recursion in x.
+// TYPE_X: out_j = sum_i post_{j,i} (.) (T^{j1} (x) T^{j2})^T (pre_i (.) in_i)
+//         FWD: recursion in x (eq. alg2c); !FWD: conjugate transpose of the recursion in p.
+// The inputs of 8-RHS subtile k+1 are copied asynchronously while subtile k is
+// computed (two staging buffers); the first copies overlap the phase setup.
+// Shared memory (float2): phases 20 Q^2 | staging 2 x 4 kRS Q^2 | intermediate 8 kRS Q^2.
 // ---------------------------------------------------------------------------
-template <int Q, bool FWD>
-__global__ void __launch_bounds__(32 * Q) k32_trans_p(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm,
+template <int Q, bool TYPE_P, bool FWD>
+__global__ void __launch_bounds__(32 * Q, 2) k32_trans(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm,
                                                        const float2 *__restrict__ in, float2 *__restrict__ out) {
   constexpr int Q2 = Q * Q;
+  constexpr int SUB = 4 * kRS * Q2;  // one staging buffer
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *pre_s = (float2 *)smem_raw;       // [4 j][4 i][Q2]
-  float2 *post_s = pre_s + 16 * Q2;         // [4 j][Q2]
-  float2 *io_s = post_s + 4 * Q2;           // [4][kRS][Q2]
-  float2 *z_s = io_s + 4 * kRS * Q2;        // [4 j][2 i1][kRS][Q2]
+  float2 *ph_s = (float2 *)smem_raw;  // TYPE_P: pre [4 j][4 i], post [4 j]; TYPE_X: pre [4 i], post [4 j][4 i]
+  float2 *io_s = ph_s + 20 * Q2;      // [2][4][kRS][Q2]
+  float2 *z_s = io_s + 2 * SUB;       // [4][2][kRS][Q2]
+  float2 *pre_s = ph_s;
+  float2 *post_s = TYPE_P ? ph_s + 16 * Q2 : ph_s + 4 * Q2;
   const int l = g.l, lb = g.L - g.l, e = g.e;
-  const long long unit = blockIdx.x;
-  const UnitIdx d = unit_decode(unit, l, lb, e);
+  const UnitIdx d = unit_decode(blockIdx.x, l, lb, e);
   const int r0 = blockIdx.y * kRMax;
   const int rc = min(kRMax, g.nrhs - r0);
+  const int nsub = (rc + kRS - 1) / kRS;
   const long long nrq = (long long)g.nrhs * Q2;
+  // inputs come from the children of B (forward) or of A (conjugate transposes)
+  auto in_pair = [&](int i) { return FWD ? pair_child_b(d, i, lb, e) : pair_child_a(d, i, l, lb, e); };
+  auto out_pair = [&](int j) { return FWD ? pair_child_a(d, j, l, lb, e) : pair_child_b(d, j, lb, e); };
+  auto issue = [&](int k) {
+    if (k < nsub) {
+      const int rs0 = k * kRS, rs = min(kRS, rc - rs0);
+      float2 *buf = io_s + (k & 1) * SUB;
+      for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
+        const int i = idx / (rs * Q2), kk = idx % (rs * Q2);
+        cp_async8(buf + i * kRS * Q2 + kk, in + in_pair(i) * nrq + (long long)(r0 + rs0) * Q2 + kk);
+      }
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  issue(1);
 
-  // phase factors of the unit, shared by all right-hand sides
-  if (FWD) {
-    // pre[j=sigma][i=c] = ec[sigma][c], post[j=sigma] = conj ep[sigma]
+  // phase factors of the unit, shared by all right-hand sides (scratch: z_s)
+  if (TYPE_P && FWD) {  // pre[j=sigma][i=c] = ec[sigma][c], post[j=sigma] = conj ep[sigma]
     family_centres<Q>(tb, tf, ph, d, l, lb, pre_s, post_s, (unsigned char *)z_s);
     for (int idx = threadIdx.x; idx < 4 * Q2; idx += blockDim.x) post_s[idx] = conjf2(post_s[idx]);
-  } else {
-    // pre[j=c][i=sigma] = conj ea[sigma][c], post[j=c] = eq[c]
-    float2 *ea = z_s;  // the intermediate buffer holds ea until the subtile loop starts
-    family_nodes<Q>(tb, tf, ph, d, l, lb, ea, post_s, (unsigned char *)io_s);
+  } else if (TYPE_P) {  // pre[j=c][i=sigma] = conj ea[sigma][c], post[j=c] = eq[c]
+    float2 *ea = z_s;
+    family_nodes<Q>(tb, tf, ph, d, l, lb, ea, post_s, (unsigned char *)(z_s + 16 * Q2));
     for (int idx = threadIdx.x; idx < 16 * Q2; idx += blockDim.x) {
       const int sg = idx / (4 * Q2), c = (idx / Q2) & 3, t = idx % Q2;
       pre_s[(c * 4 + sg) * Q2 + t] = conjf2(ea[idx]);
     }
-  }
-  __syncthreads();
-
-  for (int rs0 = 0; rs0 < rc; rs0 += kRS) {
-    const int rs = min(kRS, rc - rs0);
-    // stage the four input blocks of this subtile
-    for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
-      const int i = idx / (rs * Q2), k = idx % (rs * Q2);
-      const long long pr = FWD ? pair_child_b(d, i, lb, e) : pair_child_a(d, i, l, lb, e);
-      io_s[i * kRS * Q2 + k] = in[pr * nrq + (long long)(r0 + rs0) * Q2 + k];
-    }
-    __syncthreads();
-    // Z_{j,i1}[t'1][t2] = sum_{i2,t'2} T^{i2}[t2][t'2] (pre (.) in)_{(i1,i2)}[t'1][t'2]
-    for (int task = threadIdx.x; task < 8 * kRS * Q; task += blockDim.x) {
-      const int tp1 = task % Q, r = (task / Q) % kRS, i1 = (task / (Q * kRS)) & 1, j = task / (2 * Q * kRS);
-      if (r >= rs) continue;
-      float2 s[2][Q];
-#pragma unroll
-      for (int i2 = 0; i2 < 2; i2++)
-#pragma unroll
-        for (int tp2 = 0; tp2 < Q; tp2++) {
-          const int i = i1 * 2 + i2;
-          s[i2][tp2] = cmul(pre_s[(j * 4 + i) * Q2 + tp1 * Q + tp2], io_s[(i * kRS + r) * Q2 + tp1 * Q + tp2]);
-        }
-      float2 *zrow = z_s + ((j * 2 + i1) * kRS + r) * Q2 + tp1 * Q;
-#pragma unroll
-      for (int t2 = 0; t2 < Q; t2++) {
-        float ax = 0.f, ay = 0.f;
-#pragma unroll
-        for (int i2 = 0; i2 < 2; i2++)
-#pragma unroll
-          for (int tp2 = 0; tp2 < Q; tp2++) {
-            ax = __fmaf_rn(tm.T[i2][t2][tp2], s[i2][tp2].x, ax);
-            ay = __fmaf_rn(tm.T[i2][t2][tp2], s[i2][tp2].y, ay);
-          }
-        zrow[t2] = make_float2(ax, ay);
-      }
-    }
-    __syncthreads();
-    // Y_j[t1][t2] = sum_{i1,t'1} T^{i1}[t1][t'1] Z_{j,i1}[t'1][t2];  out_j = post_j (.) Y_j -> io_s
-    for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
-      const int t2 = task % Q, r = (task / Q) % kRS, j = task / (Q * kRS);
-      if (r >= rs) continue;
-      float2 zc[2][Q];
-#pragma unroll
-      for (int i1 = 0; i1 < 2; i1++)
-#pragma unroll
-        for (int tp1 = 0; tp1 < Q; tp1++) zc[i1][tp1] = z_s[((j * 2 + i1) * kRS + r) * Q2 + tp1 * Q + t2];
-#pragma unroll
-      for (int t1 = 0; t1 < Q; t1++) {
-        float ax = 0.f, ay = 0.f;
-#pragma unroll
-        for (int i1 = 0; i1 < 2; i1++)
-#pragma unroll
-          for (int tp1 = 0; tp1 < Q; tp1++) {
-            ax = __fmaf_rn(tm.T[i1][t1][tp1], zc[i1][tp1].x, ax);
-            ay = __fmaf_rn(tm.T[i1][t1][tp1], zc[i1][tp1].y, ay);
-          }
-        io_s[(j * kRS + r) * Q2 + t1 * Q + t2] = cmul(post_s[j * Q2 + t1 * Q + t2], make_float2(ax, ay));
-      }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
-      const int j = idx / (rs * Q2), k = idx % (rs * Q2);
-      const long long pr = FWD ? pair_child_a(d, j, l, lb, e) : pair_child_b(d, j, lb, e);
-      out[pr * nrq + (long long)(r0 + rs0) * Q2 + k] = io_s[j * kRS * Q2 + k];
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// FP32 translation, type X (see k_trans_x): out_j = sum_i post_{j,i} (.) (T^{j1} (x) T^{j2})^T (pre_i (.) in_i)
-// FWD: recursion in x (eq. alg2c); !FWD: conjugate transpose of the recursion in p.
-// ---------------------------------------------------------------------------
-template <int Q, bool FWD>
-__global__ void __launch_bounds__(32 * Q) k32_trans_x(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm,
-                                                       const float2 *__restrict__ in, float2 *__restrict__ out) {
-  constexpr int Q2 = Q * Q;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *pre_s = (float2 *)smem_raw;   // [4 i][Q2]
-  float2 *post_s = pre_s + 4 * Q2;      // [4 j][4 i][Q2]
-  float2 *io_s = post_s + 16 * Q2;      // [4][kRS][Q2]
-  float2 *w_s = io_s + 4 * kRS * Q2;    // [4 i][2 j1][kRS][Q2]
-  const int l = g.l, lb = g.L - g.l, e = g.e;
-  const long long unit = blockIdx.x;
-  const UnitIdx d = unit_decode(unit, l, lb, e);
-  const int r0 = blockIdx.y * kRMax;
-  const int rc = min(kRMax, g.nrhs - r0);
-  const long long nrq = (long long)g.nrhs * Q2;
-
-  if (FWD) {
-    // pre[i=c] = conj eq[c], post[j=sigma][i=c] = ea[sigma][c]
-    family_nodes<Q>(tb, tf, ph, d, l, lb, post_s, pre_s, (unsigned char *)io_s);
+  } else if (FWD) {  // pre[i=c] = conj eq[c], post[j=sigma][i=c] = ea[sigma][c]
+    family_nodes<Q>(tb, tf, ph, d, l, lb, post_s, pre_s, (unsigned char *)z_s);
     for (int idx = threadIdx.x; idx < 4 * Q2; idx += blockDim.x) pre_s[idx] = conjf2(pre_s[idx]);
-  } else {
-    // pre[i=sigma] = ep[sigma], post[j=c][i=sigma] = conj ec[sigma][c]
-    float2 *ec = w_s;
-    family_centres<Q>(tb, tf, ph, d, l, lb, ec, pre_s, (unsigned char *)io_s);
+  } else {  // pre[i=sigma] = ep[sigma], post[j=c][i=sigma] = conj ec[sigma][c]
+    float2 *ec = z_s;
+    family_centres<Q>(tb, tf, ph, d, l, lb, ec, pre_s, (unsigned char *)(z_s + 16 * Q2));
     for (int idx = threadIdx.x; idx < 16 * Q2; idx += blockDim.x) {
       const int sg = idx / (4 * Q2), c = (idx / Q2) & 3, u = idx % Q2;
       post_s[(c * 4 + sg) * Q2 + u] = conjf2(ec[idx]);
     }
   }
-  __syncthreads();
 
-  for (int rs0 = 0; rs0 < rc; rs0 += kRS) {
-    const int rs = min(kRS, rc - rs0);
-    for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
-      const int i = idx / (rs * Q2), k = idx % (rs * Q2);
-      const long long pr = FWD ? pair_child_b(d, i, lb, e) : pair_child_a(d, i, l, lb, e);
-      io_s[i * kRS * Q2 + k] = cmul(pre_s[i * Q2 + k % Q2], in[pr * nrq + (long long)(r0 + rs0) * Q2 + k]);
-    }
+  for (int k = 0; k < nsub; k++) {
+    const int rs0 = k * kRS, rs = min(kRS, rc - rs0);
+    float2 *io = io_s + (k & 1) * SUB;
+    cp_async_wait(k + 1 < nsub);
     __syncthreads();
-    // W_{i,j1}[t1][t'2] = sum_{t'1} T^{j1}[t'1][t1] S_i[t'1][t'2]
-    for (int task = threadIdx.x; task < 8 * kRS * Q; task += blockDim.x) {
-      const int tp2 = task % Q, r = (task / Q) % kRS, j1 = (task / (Q * kRS)) & 1, i = task / (2 * Q * kRS);
-      if (r >= rs) continue;
-      float2 col[Q];
+    if (TYPE_P) {
+      // Z_{j,i1}[t'1][t2] = sum_{i2,t'2} T^{i2}[t2][t'2] (pre (.) in)_{(i1,i2)}[t'1][t'2]
+      for (int task = threadIdx.x; task < 8 * kRS * Q; task += blockDim.x) {
+        const int tp1 = task % Q, r = (task / Q) % kRS, i1 = (task / (Q * kRS)) & 1, j = task / (2 * Q * kRS);
+        if (r >= rs) continue;
+        float2 sv[2][Q];
 #pragma unroll
-      for (int tp1 = 0; tp1 < Q; tp1++) col[tp1] = io_s[(i * kRS + r) * Q2 + tp1 * Q + tp2];
-      float2 *wb = w_s + ((i * 2 + j1) * kRS + r) * Q2 + tp2;
-#pragma unroll
-      for (int t1 = 0; t1 < Q; t1++) {
-        float ax = 0.f, ay = 0.f;
-#pragma unroll
-        for (int tp1 = 0; tp1 < Q; tp1++) {
-          ax = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].x, ax);
-          ay = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].y, ay);
-        }
-        wb[t1 * Q] = make_float2(ax, ay);
-      }
-    }
-    __syncthreads();
-    // out_j[t1][t2] = sum_i post_{j,i}[t1][t2] sum_{t'2} T^{j2}[t'2][t2] W_{i,j1}[t1][t'2]  -> io_s
-    for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
-      const int t1 = task % Q, r = (task / Q) % kRS, j = task / (Q * kRS);
-      if (r >= rs) continue;
-      const int j1 = j >> 1, j2 = j & 1;
-      float ax[Q], ay[Q];
-#pragma unroll
-      for (int t2 = 0; t2 < Q; t2++) ax[t2] = ay[t2] = 0.f;
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        float2 row[Q];
-#pragma unroll
-        for (int tp2 = 0; tp2 < Q; tp2++) row[tp2] = w_s[((i * 2 + j1) * kRS + r) * Q2 + t1 * Q + tp2];
-#pragma unroll
-        for (int t2 = 0; t2 < Q; t2++) {
-          float vx = 0.f, vy = 0.f;
+        for (int i2 = 0; i2 < 2; i2++)
 #pragma unroll
           for (int tp2 = 0; tp2 < Q; tp2++) {
-            vx = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].x, vx);
-            vy = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].y, vy);
+            const int i = i1 * 2 + i2;
+            sv[i2][tp2] = cmul(pre_s[(j * 4 + i) * Q2 + tp1 * Q + tp2], io[(i * kRS + r) * Q2 + tp1 * Q + tp2]);
           }
-          const float2 p = post_s[(j * 4 + i) * Q2 + t1 * Q + t2];
-          ax[t2] = __fmaf_rn(p.x, vx, __fmaf_rn(-p.y, vy, ax[t2]));
-          ay[t2] = __fmaf_rn(p.x, vy, __fmaf_rn(p.y, vx, ay[t2]));
+        float2 *zrow = z_s + ((j * 2 + i1) * kRS + r) * Q2 + tp1 * Q;
+#pragma unroll
+        for (int t2 = 0; t2 < Q; t2++) {
+          float ax = 0.f, ay = 0.f;
+#pragma unroll
+          for (int i2 = 0; i2 < 2; i2++)
+#pragma unroll
+            for (int tp2 = 0; tp2 < Q; tp2++) {
+              ax = __fmaf_rn(tm.T[i2][t2][tp2], sv[i2][tp2].x, ax);
+              ay = __fmaf_rn(tm.T[i2][t2][tp2], sv[i2][tp2].y, ay);
+            }
+          zrow[t2] = make_float2(ax, ay);
         }
       }
-      // io_s (the premodulated inputs) was last read in the W pass, so it can take the outputs
-      float2 *dst = io_s + (j * kRS + r) * Q2 + t1 * Q;
+      __syncthreads();
+      // Y_j[t1][t2] = sum_{i1,t'1} T^{i1}[t1][t'1] Z_{j,i1}[t'1][t2];  out_j = post_j (.) Y_j  -> io
+      for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
+        const int t2 = task % Q, r = (task / Q) % kRS, j = task / (Q * kRS);
+        if (r >= rs) continue;
+        float2 zc[2][Q];
 #pragma unroll
-      for (int t2 = 0; t2 < Q; t2++) dst[t2] = make_float2(ax[t2], ay[t2]);
+        for (int i1 = 0; i1 < 2; i1++)
+#pragma unroll
+          for (int tp1 = 0; tp1 < Q; tp1++) zc[i1][tp1] = z_s[((j * 2 + i1) * kRS + r) * Q2 + tp1 * Q + t2];
+#pragma unroll
+        for (int t1 = 0; t1 < Q; t1++) {
+          float ax = 0.f, ay = 0.f;
+#pragma unroll
+          for (int i1 = 0; i1 < 2; i1++)
+#pragma unroll
+            for (int tp1 = 0; tp1 < Q; tp1++) {
+              ax = __fmaf_rn(tm.T[i1][t1][tp1], zc[i1][tp1].x, ax);
+              ay = __fmaf_rn(tm.T[i1][t1][tp1], zc[i1][tp1].y, ay);
+            }
+          io[(j * kRS + r) * Q2 + t1 * Q + t2] = cmul(post_s[j * Q2 + t1 * Q + t2], make_float2(ax, ay));
+        }
+      }
+    } else {
+      // W_{i,j1}[t1][t'2] = sum_{t'1} T^{j1}[t'1][t1] (pre_i (.) in_i)[t'1][t'2]
+      for (int task = threadIdx.x; task < 8 * kRS * Q; task += blockDim.x) {
+        const int tp2 = task % Q, r = (task / Q) % kRS, j1 = (task / (Q * kRS)) & 1, i = task / (2 * Q * kRS);
+        if (r >= rs) continue;
+        float2 col[Q];
+#pragma unroll
+        for (int tp1 = 0; tp1 < Q; tp1++)
+          col[tp1] = cmul(pre_s[i * Q2 + tp1 * Q + tp2], io[(i * kRS + r) * Q2 + tp1 * Q + tp2]);
+        float2 *wb = z_s + ((i * 2 + j1) * kRS + r) * Q2 + tp2;
+#pragma unroll
+        for (int t1 = 0; t1 < Q; t1++) {
+          float ax = 0.f, ay = 0.f;
+#pragma unroll
+          for (int tp1 = 0; tp1 < Q; tp1++) {
+            ax = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].x, ax);
+            ay = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].y, ay);
+          }
+          wb[t1 * Q] = make_float2(ax, ay);
+        }
+      }
+      __syncthreads();
+      // out_j[t1][t2] = sum_i post_{j,i}[t1][t2] sum_{t'2} T^{j2}[t'2][t2] W_{i,j1}[t1][t'2]  -> io
+      for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
+        const int t1 = task % Q, r = (task / Q) % kRS, j = task / (Q * kRS);
+        if (r >= rs) continue;
+        const int j1 = j >> 1, j2 = j & 1;
+        float ax[Q], ay[Q];
+#pragma unroll
+        for (int t2 = 0; t2 < Q; t2++) ax[t2] = ay[t2] = 0.f;
+#pragma unroll 1
+        for (int i = 0; i < 4; i++) {
+          float2 row[Q];
+#pragma unroll
+          for (int tp2 = 0; tp2 < Q; tp2++) row[tp2] = z_s[((i * 2 + j1) * kRS + r) * Q2 + t1 * Q + tp2];
+          const float2 *pp = post_s + (j * 4 + i) * Q2 + t1 * Q;
+#pragma unroll
+          for (int t2 = 0; t2 < Q; t2++) {
+            float vx = 0.f, vy = 0.f;
+#pragma unroll
+            for (int tp2 = 0; tp2 < Q; tp2++) {
+              vx = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].x, vx);
+              vy = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].y, vy);
+            }
+            const float2 p = pp[t2];
+            ax[t2] = __fmaf_rn(p.x, vx, __fmaf_rn(-p.y, vy, ax[t2]));
+            ay[t2] = __fmaf_rn(p.x, vy, __fmaf_rn(p.y, vx, ay[t2]));
+          }
+        }
+        float2 *dst = io + (j * kRS + r) * Q2 + t1 * Q;  // the staged inputs were last read in the W pass
+#pragma unroll
+        for (int t2 = 0; t2 < Q; t2++) dst[t2] = make_float2(ax[t2], ay[t2]);
+      }
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
-      const int j = idx / (rs * Q2), k = idx % (rs * Q2);
-      const long long pr = FWD ? pair_child_a(d, j, l, lb, e) : pair_child_b(d, j, lb, e);
-      out[pr * nrq + (long long)(r0 + rs0) * Q2 + k] = io_s[j * kRS * Q2 + k];
+      const int j = idx / (rs * Q2), kk = idx % (rs * Q2);
+      out[out_pair(j) * nrq + (long long)(r0 + rs0) * Q2 + kk] = io[j * kRS * Q2 + kk];
     }
     __syncthreads();
+    issue(k + 2);
   }
 }
 
@@ -611,12 +598,20 @@ __global__ void __launch_bounds__(256) k32_init_adj(Tables tb, TablesF tf, Phase
 }
 
 // ---------------------------------------------------------------------------
-// FP32 termination (eq. alg2d), as k_term with df phases; one CTA per box A,
-// up to 32 RHS, the boxes B summed in a fixed order.
+// FP32 termination (eq. alg2d): one CTA per box A at level l1 = L - s and up to
+// 32 RHS; the boxes B at level s are summed in a fixed order.  Each thread owns
+// the accumulators u[r][m1][0..M) of one (r, m1) in registers for the whole sum.
+// Per B: y[r][m1][t2] = sum_t1 V[m1][t1] pre_B[t] d[r][t] (thread per (r, t2)),
+// then u[r][m1][m2] += post_B[m] sum_t2 V[m2][t2] y[r][m1][t2] (thread per (r, m1)).
+// The coefficients of B+1 are copied asynchronously during B.  Needs M = 2^s <= 8.
+// blockDim = 32 max(Q, M).
 // ---------------------------------------------------------------------------
+constexpr int kTermM = 8;
 template <int Q>
-__global__ void __launch_bounds__(256) k32_term(Tables tb, TablesF tf, Phase ph, Geom g, VMat<float, Q> vm,
-                                                 const float2 *__restrict__ st, float2 *__restrict__ u) {
+__global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term(Tables tb, TablesF tf, Phase ph, Geom g,
+                                                                          VMat<float, Q> vm,
+                                                                          const float2 *__restrict__ st,
+                                                                          float2 *__restrict__ u) {
   constexpr int Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l = g.l, lb = g.L - g.l, e = g.e;
@@ -628,71 +623,113 @@ __global__ void __launch_bounds__(256) k32_term(Tables tb, TablesF tf, Phase ph,
   const int nb2 = 1 << (lb + e);
   const int nB = (1 << lb) * nb2;
   const long long NN = 1LL << (2 * g.L);
-  float2 *acc = (float2 *)smem_raw;  // [rt][M2]
-  float2 *pre = acc + kRMax * M2;    // [Q2]
-  float2 *post = pre + Q2;           // [M2]
-  float2 *sv = post + M2;            // [rt][Q2]
-  float2 *y = sv + kRMax * Q2;       // [rt][M][Q]
-  for (int idx = threadIdx.x; idx < rt * M2; idx += blockDim.x) acc[idx] = make_float2(0.f, 0.f);
   const long long nrq = (long long)g.nrhs * Q2;
-  for (int B = 0; B < nB; B++) {
-    const int b1 = B / nb2, b2 = B % nb2;
-    const P1Node &c1 = pn1(tb, lb, b1, Q, Q);
-    const P2Node &c2 = pn2(tb, lb, b2, Q, Q);
-    const df rho = rhof(tb, tf, lb, b1, Q, Q);
-    const P2NodeF &c2f = p2f(tb, tf, lb, b2, Q, Q);
-    __syncthreads();
+  float2 *dbuf = (float2 *)smem_raw;         // [2][kRMax][Q2]
+  float2 *y = dbuf + 2 * kRMax * Q2;         // [kRMax][kTermM][Q]
+  float2 *phb = y + kRMax * kTermM * Q;      // [2][Q2 + M2]: pre then post
+  XDesc *xd = (XDesc *)(phb + 2 * (Q2 + kTermM * kTermM));  // [Q2 + M2]
+  const bool sep = ph.id == 3;
+  if (!sep)
     for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
       if (idx < Q2) {
-        pre[idx] = conjf2(e32(ph, tf, xn(tb, l, a1, idx / Q, Q), xn(tb, l, a2, idx % Q, Q), xnf(tb, tf, l, a1, idx / Q, Q),
-                              xnf(tb, tf, l, a2, idx % Q, Q), c1, c2, rho, c2f));
+        xd[idx] = xdesc(tf.ph, xnf(tb, tf, l, a1, idx / Q, Q), xnf(tb, tf, l, a2, idx % Q, Q));
       } else {
-        const int m = idx - Q2, i1 = a1 * M + m / M, i2 = a2 * M + m % M;
-        post[m] = e32(ph, tf, tb.xgrid[i1], tb.xgrid[i2], tf.xgrid[i1], tf.xgrid[i2], c1, c2, rho, c2f);
+        const int m = idx - Q2;
+        xd[idx] = xdesc(tf.ph, tf.xgrid[a1 * M + m / M], tf.xgrid[a2 * M + m % M]);
       }
     }
+  auto issue = [&](int B) {
+    if (B < nB) {
+      const float2 *src = st + ((long long)A * nB + B) * nrq + (long long)r0 * Q2;
+      float2 *dst = dbuf + (B & 1) * kRMax * Q2;
+      for (int idx = threadIdx.x; idx < rt * Q2; idx += blockDim.x) cp_async8(dst + idx, src + idx);
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  issue(1);
+  const int rr = threadIdx.x / M, m1o = threadIdx.x % M;  // accumulator owner (r, m1)
+  const bool owner = threadIdx.x < rt * M;
+  float ux[kTermM], uy[kTermM];
+#pragma unroll
+  for (int m2 = 0; m2 < kTermM; m2++) ux[m2] = uy[m2] = 0.f;
+  __syncthreads();
+  for (int B = 0; B < nB; B++) {
+    const int b1 = B / nb2, b2 = B % nb2;
+    float2 *pre = phb + (B & 1) * (Q2 + kTermM * kTermM);
+    float2 *post = pre + Q2;
+    const df rho = rhof(tb, tf, lb, b1, Q, Q);
+    const P2NodeF &c2f = p2f(tb, tf, lb, b2, Q, Q);
+    for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
+      float2 v;
+      if (sep) {
+        const XNode &x1 = idx < Q2 ? xn(tb, l, a1, idx / Q, Q) : tb.xgrid[a1 * M + (idx - Q2) / M];
+        const XNode &x2 = idx < Q2 ? xn(tb, l, a2, idx % Q, Q) : tb.xgrid[a2 * M + (idx - Q2) % M];
+        v = expi<float>(theta_xp(ph, x1, x2, pn1(tb, lb, b1, Q, Q), pn2(tb, lb, b2, Q, Q)));
+      } else {
+        v = expi_df(df_mul(rho, g_eval(tf.ph, xd[idx], c2f)));
+      }
+      if (idx < Q2) pre[idx] = conjf2(v);
+      else post[idx - Q2] = v;
+    }
+    cp_async_wait(B + 1 < nB);
     __syncthreads();
-    const float2 *src = st + ((long long)A * nB + B) * nrq + (long long)r0 * Q2;
-    for (int idx = threadIdx.x; idx < rt * Q2; idx += blockDim.x) sv[idx] = cmul(pre[idx % Q2], src[idx]);
-    __syncthreads();
-    for (int task = threadIdx.x; task < rt * M * Q; task += blockDim.x) {
-      const int t2 = task % Q, m1 = (task / Q) % M, r = task / (Q * M);
-      float ax = 0.f, ay = 0.f;
+    const float2 *dv = dbuf + (B & 1) * kRMax * Q2;
+    for (int task = threadIdx.x; task < rt * Q; task += blockDim.x) {
+      const int t2 = task % Q, r = task / Q;
+      float yx[kTermM], yy[kTermM];
+#pragma unroll
+      for (int m = 0; m < kTermM; m++) yx[m] = yy[m] = 0.f;
 #pragma unroll
       for (int t1 = 0; t1 < Q; t1++) {
-        const float2 s = sv[r * Q2 + t1 * Q + t2];
-        ax = __fmaf_rn(vm.V[m1][t1], s.x, ax);
-        ay = __fmaf_rn(vm.V[m1][t1], s.y, ay);
+        const float2 c = cmul(pre[t1 * Q + t2], dv[r * Q2 + t1 * Q + t2]);
+#pragma unroll
+        for (int m = 0; m < kTermM; m++) {
+          yx[m] = __fmaf_rn(vm.V[m][t1], c.x, yx[m]);
+          yy[m] = __fmaf_rn(vm.V[m][t1], c.y, yy[m]);
+        }
       }
-      y[(r * M + m1) * Q + t2] = make_float2(ax, ay);
+      for (int m = 0; m < M; m++) y[(r * kTermM + m) * Q + t2] = make_float2(yx[m], yy[m]);
     }
     __syncthreads();
-    for (int task = threadIdx.x; task < rt * M2; task += blockDim.x) {
-      const int m = task % M2, r = task / M2, m1 = m / M, m2 = m % M;
-      float ax = 0.f, ay = 0.f;
+    issue(B + 2);
+    if (owner) {
+      float2 yr[Q];
 #pragma unroll
-      for (int t2 = 0; t2 < Q; t2++) {
-        const float2 s = y[(r * M + m1) * Q + t2];
-        ax = __fmaf_rn(vm.V[m2][t2], s.x, ax);
-        ay = __fmaf_rn(vm.V[m2][t2], s.y, ay);
+      for (int t2 = 0; t2 < Q; t2++) yr[t2] = y[(rr * kTermM + m1o) * Q + t2];
+#pragma unroll
+      for (int m2 = 0; m2 < kTermM; m2++) {
+        if (m2 < M) {
+          float wx = 0.f, wy = 0.f;
+#pragma unroll
+          for (int t2 = 0; t2 < Q; t2++) {
+            wx = __fmaf_rn(vm.V[m2][t2], yr[t2].x, wx);
+            wy = __fmaf_rn(vm.V[m2][t2], yr[t2].y, wy);
+          }
+          const float2 p = post[m1o * M + m2];
+          ux[m2] = __fmaf_rn(p.x, wx, __fmaf_rn(-p.y, wy, ux[m2]));
+          uy[m2] = __fmaf_rn(p.x, wy, __fmaf_rn(p.y, wx, uy[m2]));
+        }
       }
-      const float2 p = cmul(post[m], make_float2(ax, ay));
-      const float2 a_ = acc[task];
-      acc[task] = make_float2(a_.x + p.x, a_.y + p.y);
     }
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < rt * M2; idx += blockDim.x) {
-    const int m = idx % M2, r = idx / M2;
-    const long long i1 = (long long)a1 * M + m / M, i2 = (long long)a2 * M + m % M;
-    u[(long long)(r0 + r) * NN + (i1 << g.L) + i2] = acc[idx];
+  if (owner) {
+    const long long i1 = (long long)a1 * M + m1o;
+    for (int m2 = 0; m2 < M; m2++) {
+      const long long i2 = (long long)a2 * M + m2;
+      u[(long long)(r0 + rr) * NN + (i1 << g.L) + i2] = make_float2(ux[m2], uy[m2]);
+    }
   }
 }
 
-// FP32 conjugate transpose of the termination (see k_term_adj).
+// FP32 conjugate transpose of the termination: for each B at level s (fixed order),
+//   d^{AB}[r][t] = post_B[t] sum_{m1,m2} V[m1][t1] V[m2][t2] pre_B[m] g[r][m],
+// pre_B[m] = e^{-2 pi i theta(x_m, p0(B))}, post_B[t] = e^{2 pi i theta(x^A_t, p0(B))}.
 template <int Q>
-__global__ void __launch_bounds__(256) k32_term_adj(Tables tb, TablesF tf, Phase ph, Geom g, VMat<float, Q> vm,
-                                                     const float2 *__restrict__ gin, float2 *__restrict__ st) {
+__global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term_adj(Tables tb, TablesF tf, Phase ph,
+                                                                              Geom g, VMat<float, Q> vm,
+                                                                              const float2 *__restrict__ gin,
+                                                                              float2 *__restrict__ st) {
   constexpr int Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l = g.l, lb = g.L - g.l, e = g.e;
@@ -704,58 +741,80 @@ __global__ void __launch_bounds__(256) k32_term_adj(Tables tb, TablesF tf, Phase
   const int nb2 = 1 << (lb + e);
   const int nB = (1 << lb) * nb2;
   const long long NN = 1LL << (2 * g.L);
-  float2 *gv = (float2 *)smem_raw;  // [rt][M2]
-  float2 *pre = gv + kRMax * M2;    // [M2]
-  float2 *post = pre + M2;          // [Q2]
-  float2 *gm = post + Q2;           // [rt][M2]
-  float2 *y = gm + kRMax * M2;      // [rt][Q][M]
+  const long long nrq = (long long)g.nrhs * Q2;
+  float2 *gv = (float2 *)smem_raw;            // [kRMax][M2]
+  float2 *y = gv + kRMax * kTermM * kTermM;   // [kRMax][Q][kTermM]
+  float2 *pre = y + kRMax * Q * kTermM;       // [M2]
+  float2 *post = pre + kTermM * kTermM;       // [Q2]
+  XDesc *xd = (XDesc *)(post + Q2);           // [Q2 + M2]
+  const bool sep = ph.id == 3;
   for (int idx = threadIdx.x; idx < rt * M2; idx += blockDim.x) {
     const int m = idx % M2, r = idx / M2;
     const long long i1 = (long long)a1 * M + m / M, i2 = (long long)a2 * M + m % M;
     gv[idx] = gin[(long long)(r0 + r) * NN + (i1 << g.L) + i2];
   }
-  const long long nrq = (long long)g.nrhs * Q2;
+  if (!sep)
+    for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
+      if (idx < Q2) {
+        xd[idx] = xdesc(tf.ph, xnf(tb, tf, l, a1, idx / Q, Q), xnf(tb, tf, l, a2, idx % Q, Q));
+      } else {
+        const int m = idx - Q2;
+        xd[idx] = xdesc(tf.ph, tf.xgrid[a1 * M + m / M], tf.xgrid[a2 * M + m % M]);
+      }
+    }
+  __syncthreads();
   for (int B = 0; B < nB; B++) {
     const int b1 = B / nb2, b2 = B % nb2;
-    const P1Node &c1 = pn1(tb, lb, b1, Q, Q);
-    const P2Node &c2 = pn2(tb, lb, b2, Q, Q);
     const df rho = rhof(tb, tf, lb, b1, Q, Q);
     const P2NodeF &c2f = p2f(tb, tf, lb, b2, Q, Q);
-    __syncthreads();
     for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
-      if (idx < M2) {
-        const int i1 = a1 * M + idx / M, i2 = a2 * M + idx % M;
-        pre[idx] = conjf2(e32(ph, tf, tb.xgrid[i1], tb.xgrid[i2], tf.xgrid[i1], tf.xgrid[i2], c1, c2, rho, c2f));
+      float2 v;
+      if (sep) {
+        const XNode &x1 = idx < Q2 ? xn(tb, l, a1, idx / Q, Q) : tb.xgrid[a1 * M + (idx - Q2) / M];
+        const XNode &x2 = idx < Q2 ? xn(tb, l, a2, idx % Q, Q) : tb.xgrid[a2 * M + (idx - Q2) % M];
+        v = expi<float>(theta_xp(ph, x1, x2, pn1(tb, lb, b1, Q, Q), pn2(tb, lb, b2, Q, Q)));
       } else {
-        const int t = idx - M2;
-        post[t] = e32(ph, tf, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q), xnf(tb, tf, l, a1, t / Q, Q),
-                      xnf(tb, tf, l, a2, t % Q, Q), c1, c2, rho, c2f);
+        v = expi_df(df_mul(rho, g_eval(tf.ph, xd[idx], c2f)));
       }
+      if (idx < Q2) post[idx] = v;
+      else pre[idx - Q2] = conjf2(v);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < rt * M2; idx += blockDim.x) gm[idx] = cmul(pre[idx % M2], gv[idx]);
-    __syncthreads();
-    for (int task = threadIdx.x; task < rt * Q * M; task += blockDim.x) {
-      const int m2 = task % M, t1 = (task / M) % Q, r = task / (M * Q);
-      float ax = 0.f, ay = 0.f;
+    // y[r][t1][m2] = sum_m1 V[m1][t1] pre[m] g[r][m]   (thread per (r, m2))
+    for (int task = threadIdx.x; task < rt * M; task += blockDim.x) {
+      const int m2 = task % M, r = task / M;
+      float yx[Q], yy[Q];
+#pragma unroll
+      for (int t1 = 0; t1 < Q; t1++) yx[t1] = yy[t1] = 0.f;
       for (int m1 = 0; m1 < M; m1++) {
-        const float2 s = gm[r * M2 + m1 * M + m2];
-        ax = __fmaf_rn(vm.V[m1][t1], s.x, ax);
-        ay = __fmaf_rn(vm.V[m1][t1], s.y, ay);
+        const float2 c = cmul(pre[m1 * M + m2], gv[r * M2 + m1 * M + m2]);
+#pragma unroll
+        for (int t1 = 0; t1 < Q; t1++) {
+          yx[t1] = __fmaf_rn(vm.V[m1][t1], c.x, yx[t1]);
+          yy[t1] = __fmaf_rn(vm.V[m1][t1], c.y, yy[t1]);
+        }
       }
-      y[(r * Q + t1) * M + m2] = make_float2(ax, ay);
+#pragma unroll
+      for (int t1 = 0; t1 < Q; t1++) y[(r * Q + t1) * kTermM + m2] = make_float2(yx[t1], yy[t1]);
     }
     __syncthreads();
+    // d[r][t1][t2] = post[t] sum_m2 V[m2][t2] y[r][t1][m2]   (thread per (r, t1))
     float2 *dst = st + ((long long)A * nB + B) * nrq + (long long)r0 * Q2;
-    for (int task = threadIdx.x; task < rt * Q2; task += blockDim.x) {
-      const int t = task % Q2, r = task / Q2, t1 = t / Q, t2 = t % Q;
-      float ax = 0.f, ay = 0.f;
-      for (int m2 = 0; m2 < M; m2++) {
-        const float2 s = y[(r * Q + t1) * M + m2];
-        ax = __fmaf_rn(vm.V[m2][t2], s.x, ax);
-        ay = __fmaf_rn(vm.V[m2][t2], s.y, ay);
+    for (int task = threadIdx.x; task < rt * Q; task += blockDim.x) {
+      const int t1 = task % Q, r = task / Q;
+      float2 yr[kTermM];
+#pragma unroll
+      for (int m2 = 0; m2 < kTermM; m2++) yr[m2] = m2 < M ? y[(r * Q + t1) * kTermM + m2] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int t2 = 0; t2 < Q; t2++) {
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int m2 = 0; m2 < kTermM; m2++) {
+          ax = __fmaf_rn(vm.V[m2][t2], yr[m2].x, ax);
+          ay = __fmaf_rn(vm.V[m2][t2], yr[m2].y, ay);
+        }
+        dst[r * Q2 + t1 * Q + t2] = cmul(post[t1 * Q + t2], make_float2(ax, ay));
       }
-      dst[task] = cmul(post[t], make_float2(ax, ay));
     }
   }
 }

@@ -112,18 +112,12 @@ template <typename R, int Q> struct Runner {
         const long long nunits = (1LL << (2 * (l - 1))) * nb_at(p.L - l);
         const Geom g = geom(l, kRMax, 1, nunits);
         dim3 grid((unsigned)nunits, (unsigned)((nrhs + kRMax - 1) / kRMax));
-        const int smem = (20 + 12 * kRS) * Q2 * (int)sizeof(float2);
+        const int smem = (20 + 16 * kRS) * Q2 * (int)sizeof(float2);
         if (count_only) return check();
         pre(TYPE_P ? (FWD ? K_TRANS_P : K_TRANS_P_ADJ) : (FWD ? K_TRANS_X : K_TRANS_X_ADJ));
-        if (TYPE_P) {
-          auto k = k32_trans_p<Q, FWD>;
-          set_smem(k, p.smem_optin);
-          k<<<grid, 32 * Q, smem, st>>>(p.tb, p.tf, p.ph, g, tmat(), (const float2 *)in, (float2 *)out);
-        } else {
-          auto k = k32_trans_x<Q, FWD>;
-          set_smem(k, p.smem_optin);
-          k<<<grid, 32 * Q, smem, st>>>(p.tb, p.tf, p.ph, g, tmat(), (const float2 *)in, (float2 *)out);
-        }
+        auto k = k32_trans<Q, TYPE_P, FWD>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, 32 * Q, smem, st>>>(p.tb, p.tf, p.ph, g, tmat(), (const float2 *)in, (float2 *)out);
         return check();
       }
     }
@@ -253,8 +247,9 @@ template <typename R, int Q> struct Runner {
   int term(const CT *in, CT *u) {
     const int M = 1 << p.s, M2 = M * M;
     if constexpr (sizeof(R) == 4) {
-      const int b32 = (kRMax * M2 + Q2 + M2 + kRMax * Q2 + kRMax * M * Q) * 8;
-      if (fast32() && b32 <= p.smem_optin) {
+      const int b32 = (2 * kRMax * Q2 + kRMax * kTermM * Q + 2 * (Q2 + kTermM * kTermM)) * 8 +
+                      (Q2 + M2) * (int)sizeof(XDesc);
+      if (fast32() && M <= kTermM && b32 <= p.smem_optin) {
         const long long nA = 1LL << (2 * p.l1);
         const Geom g = geom(p.l1, kRMax, 1, nA);
         dim3 grid((unsigned)nA, (unsigned)((nrhs + kRMax - 1) / kRMax));
@@ -262,7 +257,7 @@ template <typename R, int Q> struct Runner {
         pre(K_TERM);
         auto k = k32_term<Q>;
         set_smem(k, p.smem_optin);
-        k<<<grid, 256, b32, st>>>(p.tb, p.tf, p.ph, g, vmat(), (const float2 *)in, (float2 *)u);
+        k<<<grid, 32 * std::max(Q, kTermM), b32, st>>>(p.tb, p.tf, p.ph, g, vmat(), (const float2 *)in, (float2 *)u);
         return check();
       }
     }
@@ -284,8 +279,9 @@ template <typename R, int Q> struct Runner {
   int term_adj(const CT *g_in, CT *out) {
     const int M = 1 << p.s, M2 = M * M;
     if constexpr (sizeof(R) == 4) {
-      const int b32 = (2 * kRMax * M2 + M2 + Q2 + kRMax * Q * M) * 8;
-      if (fast32() && b32 <= p.smem_optin) {
+      const int b32 = (kRMax * kTermM * kTermM + kRMax * Q * kTermM + kTermM * kTermM + Q2) * 8 +
+                      (Q2 + M2) * (int)sizeof(XDesc);
+      if (fast32() && M <= kTermM && b32 <= p.smem_optin) {
         const long long nA = 1LL << (2 * p.l1);
         const Geom g = geom(p.l1, kRMax, 1, nA);
         dim3 grid((unsigned)nA, (unsigned)((nrhs + kRMax - 1) / kRMax));
@@ -293,7 +289,8 @@ template <typename R, int Q> struct Runner {
         pre(K_TERM_ADJ);
         auto k = k32_term_adj<Q>;
         set_smem(k, p.smem_optin);
-        k<<<grid, 256, b32, st>>>(p.tb, p.tf, p.ph, g, vmat(), (const float2 *)g_in, (float2 *)out);
+        k<<<grid, 32 * std::max(Q, kTermM), b32, st>>>(p.tb, p.tf, p.ph, g, vmat(), (const float2 *)g_in,
+                                                       (float2 *)out);
         return check();
       }
     }
