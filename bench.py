@@ -240,6 +240,7 @@ def run_ours(args, rank, world, dist):
     ms32 = tmax(a.elapsed_time(b) / args.steps)
     prof = plan.profile_read()
     launches_per_step = plan.kernel_launches(NRHS)
+    switch_impl = plan.info.switch_impl
     u32 = u[0].cpu().numpy()
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
@@ -315,6 +316,7 @@ def run_ours(args, rank, world, dist):
                 "h2d_bytes_per_step": N * N * NRHS * 8, "d2h_bytes_per_step": N * N * NRHS * 8,
                 "api": "fio_apply_host (pinned host buffers)"},
         "gpu_launches": launches_per_step * args.steps,
+        "switch_kernel": ["fp32_fma", "tcgen05_tf32"][switch_impl] + " (plan autotuner)",
         "kernels": kernels,
         "roofline": roof,
         "peak_probes": probes,

@@ -80,6 +80,8 @@ enum { FIO_PHASE_LINEAR = 0, FIO_PHASE_ELLIPSE = 1, FIO_PHASE_CIRCLE = 2, FIO_PH
  *   e         angular refinement of the T_P boxes: a box at level j has width
  *             2^-j in p1 and 2^-(j+e) in p2 (-1 = 2; 0 is the square-box
  *             statement of Sec. 1.1; 0 <= e <= 4)
+ * For FIO_F32 it also times the two switch kernels (FP32 FMA and tensor-core)
+ * once on its own buffers and keeps the faster (fio_plan_info().switch_impl).
  * Allocates device memory on the current CUDA device; the plan may only be
  * used with that device current.  Returns FIO_EINVAL for bad arguments,
  * FIO_ENOMEM when the state does not fit, FIO_EDEVICE without a device.
@@ -128,10 +130,23 @@ typedef struct {
   long long state_bytes;   /* device bytes of the two state buffers */
   long long table_bytes;   /* device bytes of the plan's tables */
   int max_box_sources;     /* most sources in one initialization box B */
+  int switch_impl;         /* FIO_F32: switch kernel chosen by fio_plan's autotuner,
+                              0 = FP32 FMA, 1 = tensor cores (tcgen05, split TF32) */
 } fio_plan_info_t;
 
 /* fio_plan_info -- copy the plan's parameters and sizes into *info. */
 int fio_plan_info(fio_plan_t plan, fio_plan_info_t *info);
+
+/* fio_check -- synchronise the stream and report device-side failures of earlier
+ * applies with this plan: FIO_ETIMEOUT if a kernel's bounded wait on the tensor
+ * cores expired (that apply's output is invalid; the flag is then cleared),
+ * FIO_OK otherwise.  fio_apply_host calls it itself. */
+int fio_check(fio_plan_t plan, void *stream);
+
+/* fio_plan_set_switch -- override the autotuner's choice of the FIO_F32 switch
+ * kernel: impl 0 = FP32 FMA, 1 = tensor cores.  FIO_EINVAL if the plan is FIO_F64
+ * or the tensor-core kernel does not fit this plan (its shared memory need). */
+int fio_plan_set_switch(fio_plan_t plan, int impl);
 
 /* fio_kernel_launches -- number of kernels one fio_apply (adjoint != 0: fio_apply_adjoint)
  * with nrhs right-hand sides enqueues. */

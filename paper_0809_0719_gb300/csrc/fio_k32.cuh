@@ -156,6 +156,32 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// Copy n float2 from global to shared (both 8-byte aligned) asynchronously, 16 bytes
+// at a time when the global side allows it (the shared side is 16-byte aligned).
+__device__ __forceinline__ void cp_async_run(float2 *dst, const float2 *src, int n) {
+  if ((((uintptr_t)src) & 15) == 0) {
+    const int n2 = n >> 1;
+    for (int k = threadIdx.x; k < n2; k += blockDim.x) cp_async16(dst + 2 * k, src + 2 * k);
+    if ((n & 1) && threadIdx.x == 0) cp_async8(dst + n - 1, src + n - 1);
+  } else {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cp_async8(dst + k, src + k);
+  }
+}
+// Store n float2 from shared (16-byte aligned) to global, 16 bytes at a time when aligned.
+__device__ __forceinline__ void store_run(float2 *dst, const float2 *src, int n) {
+  if ((((uintptr_t)dst) & 15) == 0) {
+    const int n2 = n >> 1;
+    for (int k = threadIdx.x; k < n2; k += blockDim.x)
+      reinterpret_cast<float4 *>(dst)[k] = reinterpret_cast<const float4 *>(src)[k];
+    if ((n & 1) && threadIdx.x == 0) dst[n - 1] = src[n - 1];
+  } else {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+  }
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait(int pending) {
   if (pending) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
@@ -196,10 +222,9 @@ __global__ void __launch_bounds__(32 * Q, 2) k32_trans(Tables tb, TablesF tf, Ph
     if (k < nsub) {
       const int rs0 = k * kRS, rs = min(kRS, rc - rs0);
       float2 *buf = io_s + (k & 1) * SUB;
-      for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
-        const int i = idx / (rs * Q2), kk = idx % (rs * Q2);
-        cp_async8(buf + i * kRS * Q2 + kk, in + in_pair(i) * nrq + (long long)(r0 + rs0) * Q2 + kk);
-      }
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        cp_async_run(buf + i * kRS * Q2, in + in_pair(i) * nrq + (long long)(r0 + rs0) * Q2, rs * Q2);
     }
     cp_async_commit();
   };
@@ -285,64 +310,79 @@ __global__ void __launch_bounds__(32 * Q, 2) k32_trans(Tables tb, TablesF tf, Ph
         }
       }
     } else {
-      // W_{i,j1}[t1][t'2] = sum_{t'1} T^{j1}[t'1][t1] (pre_i (.) in_i)[t'1][t'2]
-      for (int task = threadIdx.x; task < 8 * kRS * Q; task += blockDim.x) {
-        const int tp2 = task % Q, r = (task / Q) % kRS, j1 = (task / (Q * kRS)) & 1, i = task / (2 * Q * kRS);
+      // W_{i,j1}[t1][t'2] = sum_{t'1} T^{j1}[t'1][t1] (pre_i (.) in_i)[t'1][t'2], both j1 per task
+      for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
+        const int tp2 = task % Q, r = (task / Q) % kRS, i = task / (Q * kRS);
         if (r >= rs) continue;
         float2 col[Q];
 #pragma unroll
         for (int tp1 = 0; tp1 < Q; tp1++)
           col[tp1] = cmul(pre_s[i * Q2 + tp1 * Q + tp2], io[(i * kRS + r) * Q2 + tp1 * Q + tp2]);
-        float2 *wb = z_s + ((i * 2 + j1) * kRS + r) * Q2 + tp2;
 #pragma unroll
-        for (int t1 = 0; t1 < Q; t1++) {
-          float ax = 0.f, ay = 0.f;
+        for (int j1 = 0; j1 < 2; j1++) {
+          float2 *wb = z_s + ((i * 2 + j1) * kRS + r) * Q2 + tp2;
 #pragma unroll
-          for (int tp1 = 0; tp1 < Q; tp1++) {
-            ax = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].x, ax);
-            ay = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].y, ay);
+          for (int t1 = 0; t1 < Q; t1++) {
+            float ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int tp1 = 0; tp1 < Q; tp1++) {
+              ax = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].x, ax);
+              ay = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].y, ay);
+            }
+            wb[t1 * Q] = make_float2(ax, ay);
           }
-          wb[t1 * Q] = make_float2(ax, ay);
         }
       }
       __syncthreads();
-      // out_j[t1][t2] = sum_i post_{j,i}[t1][t2] sum_{t'2} T^{j2}[t'2][t2] W_{i,j1}[t1][t'2]  -> io
+      // out_j[t1][t2] = sum_i post_{j,i}[t1][t2] sum_{t'2} T^{j2}[t'2][t2] W_{i,j1}[t1][t'2]  -> io.
+      // A task is (j1, r, t1, half): both j2 and two of the four i; the lane pair
+      // (half = 0, 1) exchanges partial sums so that half h finishes j2 = h.
       for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
-        const int t1 = task % Q, r = (task / Q) % kRS, j = task / (Q * kRS);
-        if (r >= rs) continue;
-        const int j1 = j >> 1, j2 = j & 1;
-        float ax[Q], ay[Q];
+        const int half = task & 1, t1 = (task >> 1) % Q, r = (task >> 1) / Q % kRS, j1 = (task >> 1) / (Q * kRS);
+        const bool live = r < rs;
+        float ax[2][Q], ay[2][Q];
 #pragma unroll
-        for (int t2 = 0; t2 < Q; t2++) ax[t2] = ay[t2] = 0.f;
+        for (int j2 = 0; j2 < 2; j2++)
+#pragma unroll
+          for (int t2 = 0; t2 < Q; t2++) ax[j2][t2] = ay[j2][t2] = 0.f;
+        if (live) {
 #pragma unroll 1
-        for (int i = 0; i < 4; i++) {
-          float2 row[Q];
+          for (int ii = 0; ii < 2; ii++) {
+            const int i = 2 * half + ii;
+            float2 row[Q];
 #pragma unroll
-          for (int tp2 = 0; tp2 < Q; tp2++) row[tp2] = z_s[((i * 2 + j1) * kRS + r) * Q2 + t1 * Q + tp2];
-          const float2 *pp = post_s + (j * 4 + i) * Q2 + t1 * Q;
+            for (int tp2 = 0; tp2 < Q; tp2++) row[tp2] = z_s[((i * 2 + j1) * kRS + r) * Q2 + t1 * Q + tp2];
 #pragma unroll
-          for (int t2 = 0; t2 < Q; t2++) {
-            float vx = 0.f, vy = 0.f;
+            for (int j2 = 0; j2 < 2; j2++) {
+              const float2 *pp = post_s + ((2 * j1 + j2) * 4 + i) * Q2 + t1 * Q;
 #pragma unroll
-            for (int tp2 = 0; tp2 < Q; tp2++) {
-              vx = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].x, vx);
-              vy = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].y, vy);
+              for (int t2 = 0; t2 < Q; t2++) {
+                float vx = 0.f, vy = 0.f;
+#pragma unroll
+                for (int tp2 = 0; tp2 < Q; tp2++) {
+                  vx = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].x, vx);
+                  vy = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].y, vy);
+                }
+                const float2 p = pp[t2];
+                ax[j2][t2] = __fmaf_rn(p.x, vx, __fmaf_rn(-p.y, vy, ax[j2][t2]));
+                ay[j2][t2] = __fmaf_rn(p.x, vy, __fmaf_rn(p.y, vx, ay[j2][t2]));
+              }
             }
-            const float2 p = pp[t2];
-            ax[t2] = __fmaf_rn(p.x, vx, __fmaf_rn(-p.y, vy, ax[t2]));
-            ay[t2] = __fmaf_rn(p.x, vy, __fmaf_rn(p.y, vx, ay[t2]));
           }
         }
-        float2 *dst = io + (j * kRS + r) * Q2 + t1 * Q;  // the staged inputs were last read in the W pass
+        float2 *dst = io + ((2 * j1 + half) * kRS + r) * Q2 + t1 * Q;  // staged inputs were last read in the W pass
 #pragma unroll
-        for (int t2 = 0; t2 < Q; t2++) dst[t2] = make_float2(ax[t2], ay[t2]);
+        for (int t2 = 0; t2 < Q; t2++) {
+          const float sx = half ? ax[0][t2] : ax[1][t2], sy = half ? ay[0][t2] : ay[1][t2];
+          const float mx = half ? ax[1][t2] : ax[0][t2], my = half ? ay[1][t2] : ay[0][t2];
+          const float ox = __shfl_xor_sync(0xffffffffu, sx, 1), oy = __shfl_xor_sync(0xffffffffu, sy, 1);
+          if (live) dst[t2] = make_float2(mx + ox, my + oy);
+        }
       }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < 4 * rs * Q2; idx += blockDim.x) {
-      const int j = idx / (rs * Q2), kk = idx % (rs * Q2);
-      out[out_pair(j) * nrq + (long long)(r0 + rs0) * Q2 + kk] = io[j * kRS * Q2 + kk];
-    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) store_run(out + out_pair(j) * nrq + (long long)(r0 + rs0) * Q2, io + j * kRS * Q2, rs * Q2);
     __syncthreads();
     issue(k + 2);
   }

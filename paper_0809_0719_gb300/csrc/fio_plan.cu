@@ -166,6 +166,7 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   d.precision = precision;
   d.nrhs_max = nrhs_max;
   cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
 
   d.ph = Phase();
   d.ph.id = phase_id;
@@ -311,7 +312,8 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   const size_t b_xF = al(xnodeF.size() * sizeof(XNodeF)), b_gF = al(xgridF.size() * sizeof(XNodeF)),
                b_p1F = al(p1nodeF.size() * sizeof(P1NodeF)), b_p2F = al(p2nodeF.size() * sizeof(P2NodeF)),
                b_sF = al(srcF.size() * sizeof(SrcF));
-  const size_t tbytes = b_x + b_p1 + b_p2 + b_g + b_s + b_f + b_w + b_o + b_xF + b_gF + b_p1F + b_p2F + b_sF;
+  const size_t b_st = 256;  // device status word
+  const size_t tbytes = b_x + b_p1 + b_p2 + b_g + b_s + b_f + b_w + b_o + b_xF + b_gF + b_p1F + b_p2F + b_sF + b_st;
   const size_t sbytes = (((size_t)NN * q * q) << e) * (size_t)nrhs_max * (precision == FIO_F64 ? 16 : 8);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
@@ -342,6 +344,10 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   d.tb.src_f = (const int *)up(srcf.data(), NN * sizeof(int), b_f);
   d.tb.src_w = (const double *)up(srcw.data(), srcw.size() * sizeof(double), b_w);
   d.tb.box_off = (const int *)up(cnt.data(), (nbox + 1) * sizeof(int), b_o);
+  {
+    const int zero[64] = {0};
+    d.status = (int *)up(zero, sizeof zero, b_st);
+  }
   d.tf = TablesF();
   if (f32) {
     d.tf.xnode = (const XNodeF *)up(xnodeF.data(), xnodeF.size() * sizeof(XNodeF), b_xF);
@@ -369,6 +375,17 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
     }
   }
   p->state_bytes = 2LL * (long long)sbytes;
+  // autotune the FP32 switch on this plan's shapes (kept for every later apply)
+  d.switch_impl = 0;
+  if (precision == FIO_F32) {
+    int impl = 0;
+    const int rc = dispatch(d, fio::RUN_TUNE, nullptr, nullptr, nrhs_max, nullptr, -1, &impl);
+    if (rc) {
+      fio_destroy(p);
+      return cuda_fail((cudaError_t)rc, "switch autotuning");
+    }
+    d.switch_impl = impl;
+  }
   *out = p;
   g_err.clear();
   return FIO_OK;
@@ -433,7 +450,7 @@ int fio_apply_host(fio_plan_t p, const void *in_host, void *out_host, int nrhs, 
   if ((ce = cudaMemcpyAsync(out_host, p->stage_buf[1], n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(ce, "cudaMemcpyAsync D2H");
   if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
-  return FIO_OK;
+  return fio_check(p, stream);
 }
 
 int fio_debug_stage(fio_plan_t p, const void *f, int stage, void *out, void *stream) {
@@ -446,7 +463,7 @@ int fio_debug_stage(fio_plan_t p, const void *f, int stage, void *out, void *str
   if (rc) return cuda_fail((cudaError_t)rc, "fio_debug_stage");
   cudaError_t ce = cudaStreamSynchronize((cudaStream_t)stream);
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
-  return FIO_OK;
+  return fio_check(p, stream);
 }
 
 int fio_plan_info(fio_plan_t p, fio_plan_info_t *info) {
@@ -468,6 +485,7 @@ int fio_plan_info(fio_plan_t p, fio_plan_info_t *info) {
   info->state_bytes = p->state_bytes;
   info->table_bytes = p->table_bytes;
   info->max_box_sources = d.maxsrc;
+  info->switch_impl = d.switch_impl;
   return FIO_OK;
 }
 
@@ -522,6 +540,37 @@ int fio_profile_read(fio_plan_t p, fio_kernel_time_t *out, int max, int *n) {
     o.launches = pr->launches[k];
     o.ms = pr->ms[k];
   }
+  return FIO_OK;
+}
+
+int fio_check(fio_plan_t p, void *stream) {
+  if (!p) return fail(FIO_EINVAL, "plan is NULL");
+  int rc = check_device(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+  int v = 0;
+  if ((ce = cudaMemcpy(&v, p->d.status, sizeof v, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(ce, "cudaMemcpy(status)");
+  if (v) {
+    const int zero = 0;
+    cudaMemcpy(p->d.status, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    return fail(FIO_ETIMEOUT, "a bounded device-side wait expired (status %d); results of that apply are invalid", v);
+  }
+  return FIO_OK;
+}
+
+int fio_plan_set_switch(fio_plan_t p, int impl) {
+  if (!p) return fail(FIO_EINVAL, "plan is NULL");
+  if (impl != 0 && impl != 1) return fail(FIO_EINVAL, "switch impl %d must be 0 or 1", impl);
+  if (p->d.precision != FIO_F32) return fail(FIO_EINVAL, "only FIO_F32 plans have a choice of switch kernel");
+  if (impl == 1) {
+    int ok = 0;
+    dispatch(p->d, fio::RUN_TC_OK, nullptr, nullptr, 1, nullptr, -1, &ok);
+    if (!ok) return fail(FIO_EINVAL, "the tensor-core switch does not fit q=%d", p->d.q);
+  }
+  p->d.switch_impl = impl;
   return FIO_OK;
 }
 

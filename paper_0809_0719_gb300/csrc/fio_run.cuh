@@ -3,7 +3,7 @@
 #pragma once
 #include <algorithm>
 
-#include "fio_k32.cuh"
+#include "fio_tc.cuh"
 
 namespace fio {
 
@@ -36,10 +36,13 @@ struct PlanDev {
   double T[2][kQMax][kQMax];
   double V[kMMax][kQMax];
   int smem_optin;
-  Prof *prof;  // NULL unless profiling was ever enabled
+  int num_sms;
+  int switch_impl;  // FP32 switch: 0 FFMA kernel, 1 tensor-core kernel (chosen by the plan's autotuner)
+  int *status;  // device status word: 1 = a bounded wait expired (read by fio_check)
+  Prof *prof;   // NULL unless profiling was ever enabled
 };
 
-enum RunKind { RUN_FWD = 0, RUN_ADJ = 1, RUN_COUNT_FWD = 2, RUN_COUNT_ADJ = 3 };
+enum RunKind { RUN_FWD = 0, RUN_ADJ = 1, RUN_COUNT_FWD = 2, RUN_COUNT_ADJ = 3, RUN_TUNE = 4, RUN_TC_OK = 5 };
 
 constexpr int kSmemTarget = 100 * 1024;  // per-CTA budget of the translation kernels
 
@@ -145,6 +148,18 @@ template <typename R, int Q> struct Runner {
 
   template <bool FWD> int sw(const CT *in, CT *out) {
     if constexpr (sizeof(R) == 4) {
+      const size_t smem_tc = TcShape<Q>::smem_bytes();
+      if (fast32() && p.switch_impl == 1 && p.status && smem_tc <= (size_t)p.smem_optin) {
+        const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
+        const Geom g = geom(p.lm, kRMax, 1, pairs);
+        dim3 grid((unsigned)std::min<long long>(pairs, 2LL * std::max(1, p.num_sms)), (unsigned)((nrhs + kRMax - 1) / kRMax));
+        if (count_only) return check();
+        pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
+        auto k = k32_switch_tc<Q, FWD>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, kTcThreads, smem_tc, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, p.status);
+        return check();
+      }
       const int smem32 = (Q2 * Q2 + 2 * kRMax * Q2) * (int)sizeof(float2);
       if (fast32() && smem32 <= p.smem_optin) {
         const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
@@ -309,6 +324,36 @@ template <typename R, int Q> struct Runner {
     return check();
   }
 
+  // Autotuner: time the FFMA and the tensor-core switch on the plan's state buffers
+  // (their contents do not matter) and return the faster implementation (0 or 1).
+  int tune_switch(PlanDev &pm) {
+    if constexpr (sizeof(R) != 4) {
+      return 0;
+    } else {
+      if (!fast32() || !p.status || TcShape<Q>::smem_bytes() > (size_t)p.smem_optin) return 0;
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      float best[2] = {1e30f, 1e30f};
+      for (int impl = 0; impl < 2; impl++) {
+        pm.switch_impl = impl;
+        for (int rep = 0; rep < 3; rep++) {
+          cudaEventRecord(a, st);
+          sw<true>((const CT *)p.state[0], (CT *)p.state[1]);
+          cudaEventRecord(b, st);
+          cudaEventSynchronize(b);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, a, b);
+          if (rep > 0) best[impl] = std::min(best[impl], ms);
+        }
+      }
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      pm.switch_impl = best[1] < best[0] ? 1 : 0;
+      return pm.switch_impl;
+    }
+  }
+
   // Forward apply; stop_stage >= 0 stops after that stage and leaves its state in *stage_out.
   int forward(const void *f, void *u, int stop_stage, const void **stage_out) {
     CT *S[2] = {(CT *)p.state[0], (CT *)p.state[1]};
@@ -362,6 +407,16 @@ int run_plan(const PlanDev &p, int kind, const void *in, void *out, int nrhs, cu
   const bool count = kind == RUN_COUNT_FWD || kind == RUN_COUNT_ADJ;
   Runner<R, Q> r(p, st, nrhs, count);
   int rc;
+  if (kind == RUN_TC_OK) {  // can this plan use the tensor-core switch?
+    if (launches)
+      *launches = sizeof(R) == 4 && p.tf.xnode && p.status && TcShape<Q>::smem_bytes() <= (size_t)p.smem_optin;
+    return 0;
+  }
+  if (kind == RUN_TUNE) {
+    const int impl = r.tune_switch(const_cast<PlanDev &>(p));
+    if (launches) *launches = impl;
+    return (int)cudaGetLastError();
+  }
   if (kind == RUN_FWD || kind == RUN_COUNT_FWD) {
     const void *snap = nullptr;
     rc = r.forward(in, out, stop_stage, &snap);

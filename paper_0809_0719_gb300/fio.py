@@ -43,7 +43,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("N", "L", "q", "s", "e", "l0", "lm", "l1", "phase_id", "precision",
                                             "nrhs_max", "nstages")] + [
         ("pairs_per_level", ctypes.c_longlong), ("state_bytes", ctypes.c_longlong),
-        ("table_bytes", ctypes.c_longlong), ("max_box_sources", ctypes.c_int)]
+        ("table_bytes", ctypes.c_longlong), ("max_box_sources", ctypes.c_int), ("switch_impl", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
             L.fio_profile.argtypes = [vp, ip]
             L.fio_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ip, ctypes.POINTER(ip)]
             L.fio_peak_probe.argtypes = [ip, ctypes.POINTER(ctypes.c_double)]
+            L.fio_plan_set_switch.argtypes = [vp, ip]
+            L.fio_check.argtypes = [vp, vp]
             L.fio_last_error.restype = ctypes.c_char_p
             _lib = L
         return _lib
@@ -154,6 +156,15 @@ class Plan:
         out = torch.empty(self.info.pairs_per_level * self.q * self.q, dtype=torch.complex128, device=f.device)
         _check(lib().fio_debug_stage(self._h, f.data_ptr(), stage, out.data_ptr(), _stream_ptr(stream)))
         return out
+
+    def set_switch(self, impl: int) -> None:
+        """fio_plan_set_switch: 0 = FP32 FMA switch kernel, 1 = tensor-core switch kernel."""
+        _check(lib().fio_plan_set_switch(self._h, int(impl)))
+        self.info.switch_impl = int(impl)
+
+    def check(self, stream=None) -> None:
+        """fio_check: synchronise and raise if a bounded device-side wait expired."""
+        _check(lib().fio_check(self._h, _stream_ptr(stream)))
 
     def kernel_launches(self, nrhs: int, adjoint: bool = False) -> int:
         return int(lib().fio_kernel_launches(self._h, nrhs, int(adjoint)))

@@ -68,11 +68,15 @@ CASES = [
 
 
 @pytest.mark.parametrize("N,q,phase,s,e", CASES)
-@pytest.mark.parametrize("prec,nrhs", [("f64", 1), ("f64", 5), ("f32", 3), ("f32", 9)])
-def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, nrhs):
+@pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 5, None), ("f32", 3, 0), ("f32", 9, 0),
+                                          ("f32", 3, 1), ("f32", 33, 1)])
+def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, nrhs, sw):
+    # sw: switch kernel of the FP32 form (0 FP32 FMA, 1 tensor cores), forced past the autotuner
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
     try:
+        if sw is not None:
+            plan.set_switch(sw)
         F = gaussian_batch(N, range(100, 100 + nrhs))
         f = torch.from_numpy(F).to(plan.dtype).cuda()
         u = plan.apply(f).cpu().numpy()
@@ -87,11 +91,13 @@ def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, 
 
 
 @pytest.mark.parametrize("N,q,phase,s,e", [(64, 5, "ellipse", 0, 2), (128, 7, "circle", 3, 2), (32, 3, "separable", 0, 1)])
-@pytest.mark.parametrize("prec,nrhs", [("f64", 1), ("f64", 3), ("f32", 10)])
-def test_adjoint_matches_oracle_adjoint(fio, oracle, N, q, phase, s, e, prec, nrhs):
+@pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 3, None), ("f32", 10, 0), ("f32", 10, 1)])
+def test_adjoint_matches_oracle_adjoint(fio, oracle, N, q, phase, s, e, prec, nrhs, sw):
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
     try:
+        if sw is not None:
+            plan.set_switch(sw)
         G = gaussian_batch(N, range(200, 200 + nrhs))
         g = torch.from_numpy(G).to(plan.dtype).cuda()
         fb = plan.adjoint(g).cpu().numpy()
@@ -118,11 +124,13 @@ def test_every_stage_matches_oracle(fio, oracle, N, q, s, e):
         plan.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
+@pytest.mark.parametrize("prec,tol,sw", [("f64", 1e-12, None), ("f32", 1e-6, 0), ("f32", 1e-6, 1)])
 @pytest.mark.parametrize("N,q,e", [(64, 5, 2), (256, 9, 2)])
-def test_dot_test(fio, prec, tol, N, q, e):
+def test_dot_test(fio, prec, tol, sw, N, q, e):
     plan = fio.Plan(N, q, "ellipse", ELL16, prec, nrhs_max=2, e=e)
     try:
+        if sw is not None:
+            plan.set_switch(sw)
         f = torch.from_numpy(gaussian_batch(N, [1, 2])).to(plan.dtype).cuda()
         g = torch.from_numpy(gaussian_batch(N, [3, 4])).to(plan.dtype).cuda()
         Bf = plan.apply(f).to(torch.complex128)
