@@ -268,6 +268,11 @@ def run_ours(args, rank, world, dist):
                            torch))
     u64h = u64[0].cpu().numpy()
     plan64.close()
+    del f64, u64
+    torch.cuda.empty_cache()
+
+    # ---- the uneven batch of plans (every rank: replicas)
+    ub = run_uneven_batch(args, dev, with_errors=rank == 0) if args.batch else None
 
     if rank != 0:
         return
@@ -322,8 +327,58 @@ def run_ours(args, rank, world, dist):
         "peak_probes": probes,
         "cpu_baseline": base,
         "clocks": clk.summary(),
+        "uneven_batch": ub,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_uneven_batch(args, dev, with_errors=True):
+    """The uneven batch: 96 FP32 plans (N in {64, 128, 256, 512} drawn with seed 4,
+    q in {5, 7, 9}, 1-8 RHS, ellipse / c(x)|k| phases alternating) applied through
+    fio_batch_apply (one persistent launch per step and q-group, CUDA graph,
+    autotuned grids).  Returns aggregate outputs/s, per-kernel-kind times from one
+    eager profiled pass, and each plan's rel-L2 error (RHS 0) against the FP64-form
+    butterfly of the same plan parameters."""
+    import torch
+
+    from paper_0809_0719_gb300 import fio
+    from paper_0809_0719_gb300.inputs import uneven_batch_sources, uneven_batch_specs
+
+    specs = uneven_batch_specs()
+    t0 = time.perf_counter()
+    plans = [fio.Plan(sp["N"], sp["q"], sp["phase"], sp["params"], "f32", nrhs_max=sp["nrhs"]) for sp in specs]
+    batch = fio.Batch(plans, [sp["nrhs"] for sp in specs], tune=True)
+    setup_s = time.perf_counter() - t0
+    xs = [torch.from_numpy(uneven_batch_sources(sp, i)).to(torch.complex64) for i, sp in enumerate(specs)]
+    x = batch.pack([t.to(dev) for t in xs])
+    y = torch.empty_like(x)
+    ms = time_steps(lambda: batch.apply(x, out=y), args.steps, args.warmup, torch)
+    outputs = batch.offsets[-1]
+    prof = batch.profile(x)
+    rec = {"workload": "96 FP32 plans, N from {64,128,256,512} (seed 4), q from {5,7,9}, 1-8 RHS, "
+                       "ellipse[2,1,16,1] / circle[3,1,20,1] alternating, s=3 e=2",
+           "value": outputs / (ms * 1e-3), "unit": "outputs/s", "ms_per_step": ms, "outputs_per_step": outputs,
+           "plans": len(specs), "groups": batch.info.ngroups, "launches_per_step": batch.info.launches_fwd + 1,
+           "graph": "one CUDA graph per apply, groups on %s branches"
+                    % ("parallel" if batch.info.parallel_groups else "serial"),
+           "setup_s": setup_s, "tune_ms": batch.info.tune_ms,
+           "kernels": {k: {"launches": n, "ms": t} for k, (n, t) in prof.items()}}
+    ys = [t[0].cpu().numpy() for t in batch.unpack(y)]
+    batch.close()
+    for p in plans:
+        p.close()
+    del x, y
+    torch.cuda.empty_cache()
+    if with_errors:
+        errs = []
+        for i, sp in enumerate(specs):
+            p64 = fio.Plan(sp["N"], sp["q"], sp["phase"], sp["params"], "f64", nrhs_max=1)
+            u = p64.apply(xs[i][:1].to(torch.complex128).to(dev))[0].cpu().numpy()
+            p64.close()
+            errs.append(float(np.linalg.norm(ys[i] - u) / np.linalg.norm(u)))
+        rec["rel_l2_err_vs_fp64_butterfly"] = {"max": max(errs), "median": statistics.median(errs),
+                                               "per_plan": errs}
+    return rec
 
 
 def run_small(args):
@@ -351,11 +406,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default="full", choices=["full", "small"],
-                    help="small: N=256 q=9 16-RHS applies only (for profiler captures)")
+    ap.add_argument("--case", default="full", choices=["full", "small", "batch"],
+                    help="small: N=256 q=9 16-RHS applies only (for profiler captures); batch: the uneven batch only")
+    ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the uneven-batch measurement")
     args = ap.parse_args()
     if args.case == "small":
         run_small(args)
+        return
+    if args.case == "batch":
+        import torch
+
+        print(json.dumps({"case": "batch", **run_uneven_batch(args, torch.device("cuda", 0), with_errors=False)}),
+              flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

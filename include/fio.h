@@ -201,6 +201,83 @@ int fio_peak_probe(int kind, double *per_second);
 int fio_apply_noalloc(int N, int q, int phase_id, const double *params, int nparams, int precision, int s, int e,
                       const void *f, void *u, int nrhs, void *stream);
 
+/*
+ * Batches of plans.  A batch applies many FIO_F32 plans -- of different N,
+ * phases, right-hand-side counts and q -- as one unit: every butterfly step
+ * (initialization, each level of the recursions in p and x, the switch, the
+ * termination; Sec. 4) becomes ONE persistent kernel launch over the pairs of
+ * all plans of a q that take that step, and the whole schedule is captured once
+ * in a CUDA graph (one graph for fio_apply, one for fio_apply_adjoint).  Plans
+ * of different q (or s) form separate groups whose launch chains run on
+ * parallel branches of the graph.  Each plan's results are bit-identical to
+ * fio_apply / fio_apply_adjoint on that plan alone with the FP32 FMA switch
+ * (switch_impl 0); the batch never uses the tensor-core switch.
+ *
+ * Data: one packed DEVICE buffer for all inputs and one for all outputs.  Plan i
+ * occupies elements [off[i], off[i+1]) of both (complex64), laid out as
+ * fio_apply's (nrhs[i], N_i, N_i) arrays; off[0] = 0 and
+ * off[i+1] = off[i] + nrhs[i] N_i^2 (fio_batch_offsets).
+ *
+ * Ownership: the batch keeps pointers to the plans' tables and state buffers,
+ * so the plans must outlive it, and none of them may be applied (alone or in
+ * another batch) while an apply of this batch may be running.  One apply of a
+ * batch at a time: applies on different streams race on the plans' states.
+ */
+typedef struct fio_batch_s *fio_batch_t;
+
+enum {
+  FIO_BATCH_TUNE = 1,  /* time each launch at several persistent grid sizes and the
+                          graph with parallel and with serial groups; keep the fastest */
+  FIO_BATCH_SERIAL = 2 /* capture the groups one after another (no parallel branches) */
+};
+
+/*
+ * fio_batch_create -- build the schedule and the two graphs of a batch.
+ *   plans   nplans distinct FIO_F32 plans (1 <= nplans <= 4096) built on the current device,
+ *           each with 2^s <= 8
+ *   nrhs    nplans right-hand-side counts, 1 <= nrhs[i] <= that plan's nrhs_max
+ *   flags   0, FIO_BATCH_TUNE (runs every kernel a few times on scratch
+ *           buffers it allocates and frees; synchronises the device) and/or
+ *           FIO_BATCH_SERIAL (then tuning keeps the groups serial)
+ * Without FIO_BATCH_TUNE each launch uses one CTA per resident slot of every SM
+ * (occupancy x SM count, at most the launch's work) and the groups run on
+ * parallel graph branches.  Allocates a small device descriptor buffer.
+ */
+int fio_batch_create(fio_batch_t *out, int nplans, const fio_plan_t *plans, const int *nrhs, int flags);
+
+/* fio_batch_destroy -- free the batch (waits for the device). NULL is a no-op. */
+int fio_batch_destroy(fio_batch_t batch);
+
+/* fio_batch_offsets -- write the nplans + 1 element offsets off[] of the packed buffers. */
+int fio_batch_offsets(fio_batch_t batch, long long *off);
+
+/*
+ * fio_batch_apply -- apply every plan of the batch (adjoint != 0: its conjugate
+ * transpose) to its slice of `in`, writing its slice of `out`.  in, out: DEVICE
+ * pointers to packed complex64 buffers of fio_batch_offsets()[nplans] elements,
+ * 16-byte aligned, not overlapping.  Enqueues one one-thread kernel (which
+ * records in/out for the graph) and one graph launch on `stream`.
+ */
+int fio_batch_apply(fio_batch_t batch, const void *in, void *out, int adjoint, void *stream);
+
+typedef struct {
+  int nplans;
+  int ngroups;           /* distinct (q, s) */
+  int launches_fwd;      /* batched kernel launches in the forward graph (plus one io kernel per apply) */
+  int launches_adj;      /* the same for the adjoint graph */
+  int parallel_groups;   /* 1: groups on parallel graph branches, 0: one after another */
+  int tuned;             /* FIO_BATCH_TUNE was given */
+  long long total_elems; /* off[nplans] */
+  double tune_ms;        /* host time spent autotuning */
+} fio_batch_info_t;
+int fio_batch_info(fio_batch_t batch, fio_batch_info_t *info);
+
+/* fio_batch_profile -- run the batch once WITHOUT the graph, with a CUDA event
+ * pair around each launch, synchronise, and fill up to max entries {name,
+ * launches, total ms} per kernel kind ("b_init", "b_trans_p", ...), setting *n. */
+int fio_batch_profile(fio_batch_t batch, const void *in, void *out, int adjoint, void *stream, fio_kernel_time_t *times,
+                      int max, int *n);
+
 /* fio_last_error -- thread-local message of the last failing call ("" if none). */
 const char *fio_last_error(void);
 

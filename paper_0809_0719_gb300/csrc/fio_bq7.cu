@@ -1,0 +1,8 @@
+// fio_bq7.cu -- the batched (many-plan) kernels instantiated for q = 7.
+#include "fio_batch.cuh"
+
+namespace fio {
+int batch_q7(const BLaunch &L, cudaStream_t st, int smem_optin, int *blocks_per_sm, int *block) {
+  return batch_launch<7>(L, st, smem_optin, blocks_per_sm, block);
+}
+}  // namespace fio

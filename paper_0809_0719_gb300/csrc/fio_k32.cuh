@@ -199,8 +199,8 @@ __device__ __forceinline__ void cp_async_wait(int pending) {
 // Shared memory (float2): phases 20 Q^2 | staging 2 x 4 kRS Q^2 | intermediate 8 kRS Q^2.
 // ---------------------------------------------------------------------------
 template <int Q, bool TYPE_P, bool FWD>
-__global__ void __launch_bounds__(32 * Q, 2) k32_trans(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm,
-                                                       const float2 *__restrict__ in, float2 *__restrict__ out) {
+__device__ __forceinline__ void k32_trans_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g, const TMat<float, Q> &tm,
+                                               const float2 *__restrict__ in, float2 *__restrict__ out, long long bx_, int by_) {
   constexpr int Q2 = Q * Q;
   constexpr int SUB = 4 * kRS * Q2;  // one staging buffer
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(32 * Q, 2) k32_trans(Tables tb, TablesF tf, Ph
   float2 *pre_s = ph_s;
   float2 *post_s = TYPE_P ? ph_s + 16 * Q2 : ph_s + 4 * Q2;
   const int l = g.l, lb = g.L - g.l, e = g.e;
-  const UnitIdx d = unit_decode(blockIdx.x, l, lb, e);
-  const int r0 = blockIdx.y * kRMax;
+  const UnitIdx d = unit_decode(bx_, l, lb, e);
+  const int r0 = by_ * kRMax;
   const int rc = min(kRMax, g.nrhs - r0);
   const int nsub = (rc + kRS - 1) / kRS;
   const long long nrq = (long long)g.nrhs * Q2;
@@ -387,6 +387,11 @@ __global__ void __launch_bounds__(32 * Q, 2) k32_trans(Tables tb, TablesF tf, Ph
     issue(k + 2);
   }
 }
+template <int Q, bool TYPE_P, bool FWD>
+__global__ void __launch_bounds__(32 * Q, 2) k32_trans(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm,
+                                                       const float2 *__restrict__ in, float2 *__restrict__ out) {
+  k32_trans_body<Q, TYPE_P, FWD>(tb, tf, ph, g, tm, in, out, blockIdx.x, blockIdx.y);
+}
 
 // e^{2 pi i theta(x, p)} for the FP32 form: x by its two 1D node entries (FP64 and df
 // copies), p by its polar node entries.  Homogeneous phases go through df
@@ -408,12 +413,73 @@ __device__ __forceinline__ float2 e32k(const Phase &ph, const TablesF &tf, const
 // FP32 switch (eq. alg2m): one CTA per pair (A, B) at level lm and up to 32 RHS.
 //   FWD : out[t] = sum_s e(x^A_t, p^B_s) in[s];   !FWD: out[s] = sum_t conj e(x^A_t, p^B_s) in[t].
 // theta(x_t, p_s) = rho(s1) G(x_t, p2_{s2}): q^3 evaluations of G, q^4 products.
-// Contraction: each thread owns 3 output rows x 4 RHS.
+// Contraction: a task owns 3 output rows x up to 4 RHS (sw_contract).
 // ---------------------------------------------------------------------------
-constexpr int kSwOB = 3, kSwRB = 4;
+constexpr int kSwOB = 3;
+// out_s[r][o] = sum_i k_s[o][i] in_s[r][i] for o < q^2, r < rc: a task owns kSwOB rows
+// x RB RHS over the inner indices i = ks, ks + KS, ...; the KS partial sums of a
+// task sit in KS consecutive lanes and are combined with butterfly shuffles.
+template <int Q, int RB, int KS>
+__device__ __forceinline__ void sw_contract(const float2 *k_s, const float2 *in_s, float2 *out_s, int rc) {
+  constexpr int Q2 = Q * Q;
+  constexpr int NOG = (Q2 + kSwOB - 1) / kSwOB;
+  const int nrg = (rc + RB - 1) / RB;
+  const int ntask = NOG * nrg * KS;
+  for (int base = 0; base < ntask; base += blockDim.x) {  // uniform trip count: whole warps shuffle
+    const int task = base + threadIdx.x;
+    const bool live = task < ntask;
+    const int ks = task % KS, grp = task / KS;
+    const int rg = grp % nrg, og = min(grp / nrg, NOG - 1);
+    float ax[kSwOB][RB], ay[kSwOB][RB];
+#pragma unroll
+    for (int a_ = 0; a_ < kSwOB; a_++)
+#pragma unroll
+      for (int c_ = 0; c_ < RB; c_++) ax[a_][c_] = ay[a_][c_] = 0.f;
+    int orow[kSwOB], rr[RB];
+#pragma unroll
+    for (int a_ = 0; a_ < kSwOB; a_++) orow[a_] = min(og * kSwOB + a_, Q2 - 1);
+#pragma unroll
+    for (int c_ = 0; c_ < RB; c_++) rr[c_] = min(rg * RB + c_, rc - 1);
+    if (live) {
+#pragma unroll 3
+      for (int i = ks; i < Q2; i += KS) {
+        float2 kv[kSwOB], iv[RB];
+#pragma unroll
+        for (int a_ = 0; a_ < kSwOB; a_++) kv[a_] = k_s[orow[a_] * Q2 + i];
+#pragma unroll
+        for (int c_ = 0; c_ < RB; c_++) iv[c_] = in_s[rr[c_] * Q2 + i];
+#pragma unroll
+        for (int a_ = 0; a_ < kSwOB; a_++)
+#pragma unroll
+          for (int c_ = 0; c_ < RB; c_++) {
+            ax[a_][c_] = __fmaf_rn(kv[a_].x, iv[c_].x, __fmaf_rn(-kv[a_].y, iv[c_].y, ax[a_][c_]));
+            ay[a_][c_] = __fmaf_rn(kv[a_].x, iv[c_].y, __fmaf_rn(kv[a_].y, iv[c_].x, ay[a_][c_]));
+          }
+      }
+    }
+#pragma unroll
+    for (int m = 1; m < KS; m <<= 1)
+#pragma unroll
+      for (int a_ = 0; a_ < kSwOB; a_++)
+#pragma unroll
+        for (int c_ = 0; c_ < RB; c_++) {
+          ax[a_][c_] += __shfl_xor_sync(0xffffffffu, ax[a_][c_], m);
+          ay[a_][c_] += __shfl_xor_sync(0xffffffffu, ay[a_][c_], m);
+        }
+    if (live && ks == 0) {
+#pragma unroll
+      for (int a_ = 0; a_ < kSwOB; a_++)
+#pragma unroll
+        for (int c_ = 0; c_ < RB; c_++) {
+          const int o = og * kSwOB + a_, r = rg * RB + c_;
+          if (o < Q2 && r < rc) out_s[r * Q2 + o] = make_float2(ax[a_][c_], ay[a_][c_]);
+        }
+    }
+  }
+}
 template <int Q, bool FWD>
-__global__ void __launch_bounds__(256) k32_switch(Tables tb, TablesF tf, Phase ph, Geom g, const float2 *__restrict__ in,
-                                                   float2 *__restrict__ out) {
+__device__ __forceinline__ void k32_switch_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g,
+                                                const float2 *__restrict__ in, float2 *__restrict__ out, long long bx_, int by_) {
   constexpr int Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *k_s = (float2 *)smem_raw;        // [Q2 out][Q2 in]
@@ -422,13 +488,13 @@ __global__ void __launch_bounds__(256) k32_switch(Tables tb, TablesF tf, Phase p
   XDesc *xd = (XDesc *)out_s;              // [Q2]      (before the contraction)
   df *gt = (df *)(xd + Q2);                // [Q2][Q]
   const int l = g.l, lb = g.L - g.l, e = g.e;
-  const long long pr = blockIdx.x;
+  const long long pr = bx_;
   const int nb2 = 1 << (lb + e);
   const long long nBl = (1LL << lb) * nb2;
   const long long a = pr / nBl, b = pr - a * nBl;
   const int a1 = (int)(a >> l), a2 = (int)(a & ((1LL << l) - 1));
   const int b1 = (int)(b / nb2), b2 = (int)(b - (long long)b1 * nb2);
-  const int r0 = blockIdx.y * kRMax;
+  const int r0 = by_ * kRMax;
   const int rc = min(kRMax, g.nrhs - r0);
   const long long nrq = (long long)g.nrhs * Q2;
 
@@ -456,45 +522,29 @@ __global__ void __launch_bounds__(256) k32_switch(Tables tb, TablesF tf, Phase p
     }
   }
   __syncthreads();
+  // contraction blocking by RHS count: RB RHS x 3 rows per task, the inner sum
+  // split over KS lanes when there are few tasks (small rc)
   constexpr int NOG = (Q2 + kSwOB - 1) / kSwOB;
-  const int nrg = (rc + kSwRB - 1) / kSwRB;
-  for (int task = threadIdx.x; task < NOG * nrg; task += blockDim.x) {
-    const int rg = task % nrg, og = task / nrg;
-    float ax[kSwOB][kSwRB], ay[kSwOB][kSwRB];
-#pragma unroll
-    for (int a_ = 0; a_ < kSwOB; a_++)
-#pragma unroll
-      for (int c_ = 0; c_ < kSwRB; c_++) ax[a_][c_] = ay[a_][c_] = 0.f;
-    int orow[kSwOB], rr[kSwRB];
-#pragma unroll
-    for (int a_ = 0; a_ < kSwOB; a_++) orow[a_] = min(og * kSwOB + a_, Q2 - 1);
-#pragma unroll
-    for (int c_ = 0; c_ < kSwRB; c_++) rr[c_] = min(rg * kSwRB + c_, rc - 1);
-#pragma unroll 3
-    for (int i = 0; i < Q2; i++) {
-      float2 kv[kSwOB], iv[kSwRB];
-#pragma unroll
-      for (int a_ = 0; a_ < kSwOB; a_++) kv[a_] = k_s[orow[a_] * Q2 + i];
-#pragma unroll
-      for (int c_ = 0; c_ < kSwRB; c_++) iv[c_] = in_s[rr[c_] * Q2 + i];
-#pragma unroll
-      for (int a_ = 0; a_ < kSwOB; a_++)
-#pragma unroll
-        for (int c_ = 0; c_ < kSwRB; c_++) {
-          ax[a_][c_] = __fmaf_rn(kv[a_].x, iv[c_].x, __fmaf_rn(-kv[a_].y, iv[c_].y, ax[a_][c_]));
-          ay[a_][c_] = __fmaf_rn(kv[a_].x, iv[c_].y, __fmaf_rn(kv[a_].y, iv[c_].x, ay[a_][c_]));
-        }
-    }
-#pragma unroll
-    for (int a_ = 0; a_ < kSwOB; a_++)
-#pragma unroll
-      for (int c_ = 0; c_ < kSwRB; c_++) {
-        const int o = og * kSwOB + a_, r = rg * kSwRB + c_;
-        if (o < Q2 && r < rc) out_s[r * Q2 + o] = make_float2(ax[a_][c_], ay[a_][c_]);
-      }
+  const int RB = rc >= 3 ? 4 : rc;
+  int KS = 1;
+  while (KS < 8 && NOG * ((rc + RB - 1) / RB) * KS < (int)blockDim.x / 2) KS *= 2;
+  if (RB == 4) {
+    if (KS == 1) sw_contract<Q, 4, 1>(k_s, in_s, out_s, rc);
+    else if (KS == 2) sw_contract<Q, 4, 2>(k_s, in_s, out_s, rc);
+    else if (KS == 4) sw_contract<Q, 4, 4>(k_s, in_s, out_s, rc);
+    else sw_contract<Q, 4, 8>(k_s, in_s, out_s, rc);
+  } else if (RB == 2) {
+    sw_contract<Q, 2, 8>(k_s, in_s, out_s, rc);
+  } else {
+    sw_contract<Q, 1, 8>(k_s, in_s, out_s, rc);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < rc * Q2; idx += blockDim.x) out[pr * nrq + (long long)r0 * Q2 + idx] = out_s[idx];
+}
+template <int Q, bool FWD>
+__global__ void __launch_bounds__(256) k32_switch(Tables tb, TablesF tf, Phase ph, Geom g, const float2 *__restrict__ in,
+                                                   float2 *__restrict__ out) {
+  k32_switch_body<Q, FWD>(tb, tf, ph, g, in, out, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,15 +552,15 @@ __global__ void __launch_bounds__(256) k32_switch(Tables tb, TablesF tf, Phase p
 // up to 32 RHS, GA boxes A at a time.
 // ---------------------------------------------------------------------------
 template <int Q>
-__global__ void __launch_bounds__(256) k32_init(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc, int GA,
-                                                 const float2 *__restrict__ f, float2 *__restrict__ st) {
+__device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g, int maxsrc, int GA,
+                                              const float2 *__restrict__ f, float2 *__restrict__ st, long long bx_, int by_) {
   constexpr int Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l0 = g.l, lb = g.L - g.l, e = g.e;
-  const int box = blockIdx.x;
+  const int box = bx_;
   const int nb2 = 1 << (lb + e);
   const int b1 = box / nb2, b2 = box % nb2;
-  const int r0 = blockIdx.y * kRMax;
+  const int r0 = by_ * kRMax;
   const int rt = min(kRMax, g.nrhs - r0);
   const int j0 = tb.box_off[box], ns = tb.box_off[box + 1] - j0;
   const long long NN = 1LL << (2 * g.L);
@@ -566,18 +616,23 @@ __global__ void __launch_bounds__(256) k32_init(Tables tb, TablesF tf, Phase ph,
     }
   }
 }
+template <int Q>
+__global__ void __launch_bounds__(256) k32_init(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc, int GA,
+                                                 const float2 *__restrict__ f, float2 *__restrict__ st) {
+  k32_init_body<Q>(tb, tf, ph, g, maxsrc, GA, f, st, blockIdx.x, blockIdx.y);
+}
 
 // FP32 conjugate transpose of the initialization (see k_init_adj).
 template <int Q>
-__global__ void __launch_bounds__(256) k32_init_adj(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc,
-                                                     const float2 *__restrict__ st, float2 *__restrict__ fbar) {
+__device__ __forceinline__ void k32_init_adj_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g, int maxsrc,
+                                                  const float2 *__restrict__ st, float2 *__restrict__ fbar, long long bx_, int by_) {
   constexpr int Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l0 = g.l, lb = g.L - g.l, e = g.e;
-  const int box = blockIdx.x;
+  const int box = bx_;
   const int nb2 = 1 << (lb + e);
   const int b1 = box / nb2, b2 = box % nb2;
-  const int r0 = blockIdx.y * kRMax;
+  const int r0 = by_ * kRMax;
   const int rt = min(kRMax, g.nrhs - r0);
   const int j0 = tb.box_off[box], ns = tb.box_off[box + 1] - j0;
   const long long NN = 1LL << (2 * g.L);
@@ -636,6 +691,11 @@ __global__ void __launch_bounds__(256) k32_init_adj(Tables tb, TablesF tf, Phase
     fbar[(long long)(r0 + r) * NN + tb.src_f[j0 + j]] = acc[j * kRMax + r];
   }
 }
+template <int Q>
+__global__ void __launch_bounds__(256) k32_init_adj(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc,
+                                                     const float2 *__restrict__ st, float2 *__restrict__ fbar) {
+  k32_init_adj_body<Q>(tb, tf, ph, g, maxsrc, st, fbar, blockIdx.x, blockIdx.y);
+}
 
 // ---------------------------------------------------------------------------
 // FP32 termination (eq. alg2d): one CTA per box A at level l1 = L - s and up to
@@ -648,17 +708,15 @@ __global__ void __launch_bounds__(256) k32_init_adj(Tables tb, TablesF tf, Phase
 // ---------------------------------------------------------------------------
 constexpr int kTermM = 8;
 template <int Q>
-__global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term(Tables tb, TablesF tf, Phase ph, Geom g,
-                                                                          VMat<float, Q> vm,
-                                                                          const float2 *__restrict__ st,
-                                                                          float2 *__restrict__ u) {
+__device__ __forceinline__ void k32_term_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g,
+                                              const VMat<float, Q> &vm, const float2 *__restrict__ st, float2 *__restrict__ u, long long bx_, int by_) {
   constexpr int Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l = g.l, lb = g.L - g.l, e = g.e;
   const int M = 1 << g.s, M2 = M * M;
-  const int A = blockIdx.x, nA1 = 1 << l;
+  const int A = bx_, nA1 = 1 << l;
   const int a1 = A >> l, a2 = A & (nA1 - 1);
-  const int r0 = blockIdx.y * kRMax;
+  const int r0 = by_ * kRMax;
   const int rt = min(kRMax, g.nrhs - r0);
   const int nb2 = 1 << (lb + e);
   const int nB = (1 << lb) * nb2;
@@ -761,22 +819,28 @@ __global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term(Table
     }
   }
 }
+template <int Q>
+__global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term(Tables tb, TablesF tf, Phase ph, Geom g,
+                                                                          VMat<float, Q> vm,
+                                                                          const float2 *__restrict__ st,
+                                                                          float2 *__restrict__ u) {
+  k32_term_body<Q>(tb, tf, ph, g, vm, st, u, blockIdx.x, blockIdx.y);
+}
 
 // FP32 conjugate transpose of the termination: for each B at level s (fixed order),
 //   d^{AB}[r][t] = post_B[t] sum_{m1,m2} V[m1][t1] V[m2][t2] pre_B[m] g[r][m],
 // pre_B[m] = e^{-2 pi i theta(x_m, p0(B))}, post_B[t] = e^{2 pi i theta(x^A_t, p0(B))}.
 template <int Q>
-__global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term_adj(Tables tb, TablesF tf, Phase ph,
-                                                                              Geom g, VMat<float, Q> vm,
-                                                                              const float2 *__restrict__ gin,
-                                                                              float2 *__restrict__ st) {
+__device__ __forceinline__ void k32_term_adj_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g,
+                                                  const VMat<float, Q> &vm, const float2 *__restrict__ gin,
+                                                  float2 *__restrict__ st, long long bx_, int by_) {
   constexpr int Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l = g.l, lb = g.L - g.l, e = g.e;
   const int M = 1 << g.s, M2 = M * M;
-  const int A = blockIdx.x, nA1 = 1 << l;
+  const int A = bx_, nA1 = 1 << l;
   const int a1 = A >> l, a2 = A & (nA1 - 1);
-  const int r0 = blockIdx.y * kRMax;
+  const int r0 = by_ * kRMax;
   const int rt = min(kRMax, g.nrhs - r0);
   const int nb2 = 1 << (lb + e);
   const int nB = (1 << lb) * nb2;
@@ -802,11 +866,11 @@ __global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term_adj(T
         xd[idx] = xdesc(tf.ph, tf.xgrid[a1 * M + m / M], tf.xgrid[a2 * M + m % M]);
       }
     }
-  __syncthreads();
   for (int B = 0; B < nB; B++) {
     const int b1 = B / nb2, b2 = B % nb2;
     const df rho = rhof(tb, tf, lb, b1, Q, Q);
     const P2NodeF &c2f = p2f(tb, tf, lb, b2, Q, Q);
+    __syncthreads();  // gv/xd are ready; the previous B is done reading pre/post
     for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
       float2 v;
       if (sep) {
@@ -857,6 +921,13 @@ __global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term_adj(T
       }
     }
   }
+}
+template <int Q>
+__global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) k32_term_adj(Tables tb, TablesF tf, Phase ph,
+                                                                              Geom g, VMat<float, Q> vm,
+                                                                              const float2 *__restrict__ gin,
+                                                                              float2 *__restrict__ st) {
+  k32_term_adj_body<Q>(tb, tf, ph, g, vm, gin, st, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace fio

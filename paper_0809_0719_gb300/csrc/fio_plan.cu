@@ -21,24 +21,9 @@
 #include <vector>
 
 #include "fio.h"
-#include "fio_run.cuh"
+#include "fio_internal.cuh"
 
-namespace fio {
-int run_q3(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
-int run_q5(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
-int run_q7(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
-int run_q9(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
-int run_q11(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
-}  // namespace fio
 
-struct fio_plan_s {
-  fio::PlanDev d;
-  int device;
-  void *tables;
-  long long table_bytes, state_bytes;
-  void *stage_buf[2];
-  size_t stage_bytes;
-};
 
 namespace {
 

@@ -46,6 +46,11 @@ class PlanInfo(ctypes.Structure):
         ("table_bytes", ctypes.c_longlong), ("max_box_sources", ctypes.c_int), ("switch_impl", ctypes.c_int)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("nplans", "ngroups", "launches_fwd", "launches_adj", "parallel_groups",
+                                            "tuned")] + [("total_elems", ctypes.c_longlong), ("tune_ms", ctypes.c_double)]
+
+
 def lib() -> ctypes.CDLL:
     """Load libfio.so, building it first (nvcc, sm_103a) if it is missing or stale."""
     global _lib
@@ -69,6 +74,12 @@ def lib() -> ctypes.CDLL:
             L.fio_peak_probe.argtypes = [ip, ctypes.POINTER(ctypes.c_double)]
             L.fio_plan_set_switch.argtypes = [vp, ip]
             L.fio_check.argtypes = [vp, vp]
+            L.fio_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(ip), ip]
+            L.fio_batch_destroy.argtypes = [vp]
+            L.fio_batch_offsets.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+            L.fio_batch_apply.argtypes = [vp, vp, vp, ip, vp]
+            L.fio_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+            L.fio_batch_profile.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(KernelTime), ip, ctypes.POINTER(ip)]
             L.fio_last_error.restype = ctypes.c_char_p
             _lib = L
         return _lib
@@ -179,6 +190,77 @@ class Plan:
         n = ctypes.c_int()
         _check(lib().fio_profile_read(self._h, buf, 16, ctypes.byref(n)))
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(n.value)}
+
+
+class Batch:
+    """fio_batch_create over FP32 plans: one persistent launch per butterfly step and
+    q-group, replayed from a captured CUDA graph.  Inputs and outputs are packed
+    complex64 vectors; plan i occupies [offsets[i], offsets[i+1]) as its
+    (nrhs[i], N_i, N_i) array.  The plans must stay alive while the batch does."""
+
+    def __init__(self, plans, nrhs, tune: bool = False, serial: bool = False):
+        self._h = None
+        L = lib()
+        self.plans = list(plans)
+        n = len(self.plans)
+        ph = (ctypes.c_void_p * n)(*[p._h for p in self.plans])
+        nr = (ctypes.c_int * n)(*[int(r) for r in nrhs])
+        h = ctypes.c_void_p()
+        _check(L.fio_batch_create(ctypes.byref(h), n, ph, nr, (1 if tune else 0) | (2 if serial else 0)))
+        self._h = h
+        off = (ctypes.c_longlong * (n + 1))()
+        _check(L.fio_batch_offsets(h, off))
+        self.offsets = [int(v) for v in off]
+        self.nrhs = [int(r) for r in nrhs]
+        self.info = BatchInfo()
+        _check(L.fio_batch_info(h, ctypes.byref(self.info)))
+
+    def close(self) -> None:
+        if self._h is not None and _lib is not None:
+            _lib.fio_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _io(self, x: torch.Tensor, out, name: str):
+        total = self.offsets[-1]
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.complex64:
+            raise TypeError("%s must be a complex64 CUDA tensor" % name)
+        if x.numel() != total or not x.is_contiguous():
+            raise ValueError("%s must be contiguous with %d elements" % (name, total))
+        if out is None:
+            out = torch.empty(total, dtype=torch.complex64, device=x.device)
+        elif out.dtype != torch.complex64 or out.numel() != total or not out.is_contiguous() or not out.is_cuda:
+            raise ValueError("out must be a contiguous complex64 CUDA tensor with %d elements" % total)
+        return out
+
+    def apply(self, x: torch.Tensor, out: torch.Tensor | None = None, adjoint: bool = False, stream=None):
+        """fio_batch_apply on a packed buffer; returns the packed output."""
+        out = self._io(x, out, "input")
+        _check(lib().fio_batch_apply(self._h, x.data_ptr(), out.data_ptr(), int(adjoint), _stream_ptr(stream)))
+        return out
+
+    def profile(self, x: torch.Tensor, adjoint: bool = False, stream=None) -> dict:
+        """fio_batch_profile: one eager pass, {kernel kind: (launches, total ms)}."""
+        out = self._io(x, None, "input")
+        buf = (KernelTime * 16)()
+        n = ctypes.c_int()
+        _check(lib().fio_batch_profile(self._h, x.data_ptr(), out.data_ptr(), int(adjoint), _stream_ptr(stream), buf,
+                                       16, ctypes.byref(n)))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(n.value)}
+
+    def pack(self, tensors) -> torch.Tensor:
+        """Concatenate per-plan (nrhs, N, N) complex64 CUDA tensors into one packed buffer."""
+        return torch.cat([t.reshape(-1) for t in tensors]).contiguous()
+
+    def unpack(self, packed: torch.Tensor):
+        """Per-plan (nrhs, N, N) views of a packed buffer."""
+        return [packed[self.offsets[i]:self.offsets[i + 1]].view(self.nrhs[i], p.N, p.N)
+                for i, p in enumerate(self.plans)]
 
 
 def peak_probe(kind: str) -> float:

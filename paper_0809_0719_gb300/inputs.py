@@ -30,3 +30,30 @@ def sample_indices(N: int, count: int, seed: int) -> np.ndarray:
     """`count` distinct flat grid indices (i1*N + i2) drawn without replacement."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(N * N, size=min(count, N * N), replace=False)).astype(np.int64)
+
+
+ELLIPSE_16 = ("ellipse", (2.0, 1.0, 16.0, 1.0))  # c1, c2 = (2 + sin sin)/16, (2 + cos cos)/16
+CIRCLE_20 = ("circle", (3.0, 1.0, 20.0, 1.0))    # c = (3 + sin sin)/20
+
+
+def uneven_batch_specs(count: int = 96, seed: int = 4) -> list[dict]:
+    """Plans of the uneven-batch workload, one dict {N, q, nrhs, phase, params} each.
+
+    For plan i, N is drawn from (64, 128, 256, 512), then q from (5, 7, 9), then
+    nrhs from 1..8, all with numpy.random.default_rng(seed) in that order; the
+    phase alternates between the ellipse phase (even i) and the c(x)|k| phase
+    (odd i)."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        N = int(rng.choice([64, 128, 256, 512]))
+        q = int(rng.choice([5, 7, 9]))
+        nrhs = int(rng.integers(1, 9))
+        phase, params = ELLIPSE_16 if i % 2 == 0 else CIRCLE_20
+        specs.append({"N": N, "q": q, "nrhs": nrhs, "phase": phase, "params": params})
+    return specs
+
+
+def uneven_batch_sources(spec: dict, index: int) -> np.ndarray:
+    """(nrhs, N, N) complex128 sources of plan `index`: gaussian_sources(N, 10000 + 100 index + r)."""
+    return gaussian_batch(spec["N"], [10000 + 100 * index + r for r in range(spec["nrhs"])])

@@ -67,3 +67,20 @@ def test_binding_has_no_cpu_path():
     # the binding's compute calls go through the library only
     src = open(os.path.join(ROOT, "paper_0809_0719_gb300", "fio.py")).read()
     assert "oracle" not in src and "numpy" not in src
+
+
+def test_batch_calls_reject_bad_arguments_without_a_gpu(lib):
+    h = ctypes.c_void_p()
+    nr = (ctypes.c_int * 1)(1)
+    plans = (ctypes.c_void_p * 1)(None)
+    assert lib.fio_batch_create(None, 1, plans, nr, 0) == -1
+    assert lib.fio_batch_create(ctypes.byref(h), 0, plans, nr, 0) == -1      # no plans
+    assert lib.fio_batch_create(ctypes.byref(h), 5000, plans, nr, 0) == -1   # too many
+    assert lib.fio_batch_create(ctypes.byref(h), 1, None, nr, 0) == -1
+    assert lib.fio_batch_create(ctypes.byref(h), 1, plans, None, 0) == -1
+    assert lib.fio_batch_create(ctypes.byref(h), 1, plans, nr, 8) == -1      # unknown flag
+    assert len(lib.fio_last_error()) > 0
+    assert lib.fio_batch_apply(None, None, None, 0, None) == -1
+    assert lib.fio_batch_offsets(None, None) == -1
+    assert lib.fio_batch_info(None, None) == -1
+    assert lib.fio_batch_destroy(None) == 0
