@@ -253,6 +253,7 @@ def run_ours(args, rank, world, dist):
     prof = plan.profile_read()
     launches_per_step = plan.kernel_launches(NRHS)
     switch_impl = plan.info.switch_impl
+    trans_rs = plan.info.trans_rs
     u32 = u[0].cpu().numpy()
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
@@ -334,6 +335,7 @@ def run_ours(args, rank, world, dist):
                 "api": "fio_apply_host (pinned host buffers)"},
         "gpu_launches": launches_per_step * args.steps,
         "switch_kernel": ["fp32_fma", "tcgen05_tf32"][switch_impl] + " (plan autotuner)",
+        "translation_rhs_subtile": trans_rs,
         "kernels": kernels,
         "roofline": roof,
         "peak_probes": probes,
@@ -394,14 +396,14 @@ def run_uneven_batch(args, dev, with_errors=True):
 
 
 def run_small(args):
-    """--case small: only the timed applies of an N=256, q=9, 16-RHS FP32 plan (5.4 GB),
-    forward then adjoint; the case the ncu captures use."""
+    """--case small: only the timed applies of a small FP32 plan (default N=256, q=9,
+    16 RHS: 5.4 GB of state), forward then adjoint; the case the ncu captures use."""
     import torch
 
     from paper_0809_0719_gb300 import fio
     from paper_0809_0719_gb300.inputs import gaussian_batch
 
-    n, r = 256, 16
+    n, r = args.small_n, args.small_nrhs
     plan = fio.Plan(n, Q, "ellipse", PARAMS, "f32", nrhs_max=r, s=S, e=E)
     f = torch.from_numpy(gaussian_batch(n, range(r))).to(torch.complex64).cuda()
     u = torch.empty_like(f)
@@ -421,6 +423,8 @@ def main():
     ap.add_argument("--case", default="full", choices=["full", "small", "batch"],
                     help="small: N=256 q=9 16-RHS applies only (for profiler captures); batch: the uneven batch only")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the uneven-batch measurement")
+    ap.add_argument("--small-n", type=int, default=256, help="--case small: N")
+    ap.add_argument("--small-nrhs", type=int, default=16, help="--case small: right-hand sides")
     args = ap.parse_args()
     if args.case == "small":
         run_small(args)

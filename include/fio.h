@@ -80,8 +80,9 @@ enum { FIO_PHASE_LINEAR = 0, FIO_PHASE_ELLIPSE = 1, FIO_PHASE_CIRCLE = 2, FIO_PH
  *   e         angular refinement of the T_P boxes: a box at level j has width
  *             2^-j in p1 and 2^-(j+e) in p2 (-1 = 2; 0 is the square-box
  *             statement of Sec. 1.1; 0 <= e <= 4)
- * For FIO_F32 it also times the two switch kernels (FP32 FMA and tensor-core)
- * once on its own buffers and keeps the faster (fio_plan_info().switch_impl).
+ * For FIO_F32 it also times the two switch kernels (FP32 FMA and tensor-core) and
+ * two translation subtile widths once on its own buffers and keeps the faster
+ * (fio_plan_info().switch_impl, .trans_rs).
  * Allocates device memory on the current CUDA device; the plan may only be
  * used with that device current.  Returns FIO_EINVAL for bad arguments,
  * FIO_ENOMEM when the state does not fit, FIO_EDEVICE without a device.
@@ -132,6 +133,8 @@ typedef struct {
   int max_box_sources;     /* most sources in one initialization box B */
   int switch_impl;         /* FIO_F32: switch kernel chosen by fio_plan's autotuner,
                               0 = FP32 FMA, 1 = tensor cores (tcgen05, split TF32) */
+  int trans_rs;            /* FIO_F32: right-hand sides per translation subtile (4 or 8),
+                              chosen by fio_plan's autotuner */
 } fio_plan_info_t;
 
 /* fio_plan_info -- copy the plan's parameters and sizes into *info. */

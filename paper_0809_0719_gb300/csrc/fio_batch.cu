@@ -104,7 +104,7 @@ struct fio_batch_s {
 namespace {
 
 // Shared memory of each kernel kind for item set `its` of q, s (dynamic bytes).
-long long kind_smem(int kind, int q, int s, const std::vector<BWork> &its) {
+long long kind_smem(int kind, int q, int s, int rs, const std::vector<BWork> &its) {
   const long long Q2 = (long long)q * q, M2 = 1LL << (2 * s);
   const long long xd = (long long)sizeof(XDesc);
   long long b = 0;
@@ -121,9 +121,9 @@ long long kind_smem(int kind, int q, int s, const std::vector<BWork> &its) {
   case K_TRANS_P:
   case K_TRANS_X:
   case K_TRANS_P_ADJ:
-  case K_TRANS_X_ADJ: return (20 + 16 * kRS) * Q2 * 8;
+  case K_TRANS_X_ADJ: return trans32_smem_bytes(q, rs);
   case K_SWITCH:
-  case K_SWITCH_ADJ: return (Q2 * Q2 + 2 * kRMax * Q2) * 8;
+  case K_SWITCH_ADJ: return sw32_smem_bytes(q);
   case K_TERM: return (2 * kRMax * Q2 + (long long)kRMax * kTermM * q + 2 * (Q2 + kTermM * kTermM)) * 8 + (Q2 + M2) * xd;
   case K_TERM_ADJ:
     return ((long long)kRMax * kTermM * kTermM + (long long)kRMax * q * kTermM + kTermM * kTermM + Q2) * 8 +
@@ -182,8 +182,8 @@ int build_schedule(fio_batch_s *b, int adj) {
           int GA = kind == K_INIT ? std::max(1, kBatchBlockInit / (rt * d.q)) : 1;
           std::vector<BWork> one(1, w);
           one[0].GA = GA;
-          while (kind == K_INIT && kind_smem(kind, G.q, G.s, one) > budget && GA > 1) one[0].GA = --GA;
-          if (kind_smem(kind, G.q, G.s, one) > budget)
+          while (kind == K_INIT && kind_smem(kind, G.q, G.s, 8, one) > budget && GA > 1) one[0].GA = --GA;
+          if (kind_smem(kind, G.q, G.s, 8, one) > budget)
             return bfail(FIO_EINVAL, "plan %d: %d sources in one initialization box exceed the batched kernel's shared memory",
                          i, d.maxsrc);
           w.GA = GA;
@@ -219,7 +219,10 @@ int build_schedule(fio_batch_s *b, int adj) {
         its.push_back(w);
       }
       if (its.empty()) return FIO_OK;
-      const long long sm = kind_smem(kind, G.q, G.s, its);
+      int maxr = 0;
+      for (const BWork &w : its) maxr = std::max(maxr, w.g.nrhs);
+      h.L.rs = maxr <= 4 ? 4 : 8;  // translations: narrow subtiles when every plan has few RHS
+      const long long sm = kind_smem(kind, G.q, G.s, h.L.rs, its);
       if (sm > budget) return bfail(FIO_EINVAL, "q=%d: the batched kernel needs %lld B of shared memory", G.q, sm);
       h.L.smem = (int)sm;
       h.L.n = (int)its.size();
@@ -457,22 +460,33 @@ int fio_batch_create(fio_batch_t *out, int nplans, const fio_plan_t *plans, cons
     for (int adj = 0; adj < 2; adj++)
       for (auto &gl : b->sched[adj])
         for (HostLaunch &h : gl) {
-          const long long g1 = (long long)h.blocks_per_sm * b->num_sms;
-          std::vector<long long> cand = {g1, 2 * g1, 4 * g1};
-          if (h.L.total <= 8 * g1) cand.push_back(h.L.total);  // one CTA per unit
-          int best_grid = h.L.grid;
+          const bool is_trans = h.L.kind == K_TRANS_P || h.L.kind == K_TRANS_X || h.L.kind == K_TRANS_P_ADJ ||
+                                h.L.kind == K_TRANS_X_ADJ;
+          BLaunch best_l = h.L;
           float best = 1e30f;
-          for (long long c : cand) {
-            const int grid = (int)std::min<long long>(c, h.L.total);
+          for (int rs : {4, 8}) {
+            if (!is_trans && rs != h.L.rs) continue;
             BLaunch L = h.L;
-            L.grid = grid;
-            const float ms = time_ms(ts, [&]() { return batch_dispatch(L, ts, b->smem_optin, nullptr, nullptr); });
-            if (ms < best) {
-              best = ms;
-              best_grid = grid;
+            L.rs = rs;
+            if (is_trans) {
+              std::vector<BWork> none;
+              L.smem = (int)kind_smem(L.kind, L.q, L.s, rs, none);
+            }
+            int bps = 0, blk = 0;
+            if (batch_dispatch(L, nullptr, b->smem_optin, &bps, &blk) || bps < 1) continue;
+            const long long g1 = (long long)bps * b->num_sms;
+            std::vector<long long> cand = {g1, 2 * g1, 4 * g1};
+            if (L.total <= 8 * g1) cand.push_back(L.total);  // one CTA per unit
+            for (long long c : cand) {
+              L.grid = (int)std::min<long long>(c, L.total);
+              const float ms = time_ms(ts, [&]() { return batch_dispatch(L, ts, b->smem_optin, nullptr, nullptr); });
+              if (ms < best) {
+                best = ms;
+                best_l = L;
+              }
             }
           }
-          h.L.grid = best_grid;
+          h.L = best_l;
         }
     // groups on parallel branches or one after another
     if (b->groups.size() > 1 && b->parallel) {

@@ -67,17 +67,17 @@ __device__ __forceinline__ void batch_loop(const BWork *__restrict__ items, cons
   }
 }
 
-template <int Q, bool TYPE_P, bool FWD>
-__global__ void __launch_bounds__(32 * Q, 2) kb_trans(const BWork *__restrict__ items, const long long *__restrict__ start,
-                                                      int n, TMat<float, Q> tm) {
+template <int Q, bool TYPE_P, bool FWD, int RS>
+__global__ void __launch_bounds__(TransShape<Q, RS>::threads, TransShape<Q, RS>::min_blocks)
+    kb_trans(const BWork *__restrict__ items, const long long *__restrict__ start, int n, TMat<float, Q> tm) {
   __shared__ BWork w_s;
   batch_loop(items, start, n, w_s, [&](long long unit, int ry) {
-    k32_trans_body<Q, TYPE_P, FWD>(w_s.tb, w_s.tf, w_s.ph, w_s.g, tm, w_s.in, w_s.out, unit, ry);
+    k32_trans_body<Q, TYPE_P, FWD, RS>(w_s.tb, w_s.tf, w_s.ph, w_s.g, tm, w_s.in, w_s.out, unit, ry);
   });
 }
 
 template <int Q, bool FWD>
-__global__ void __launch_bounds__(256) kb_switch(const BWork *__restrict__ items, const long long *__restrict__ start,
+__global__ void __launch_bounds__(SwShape<Q>::threads, 2) kb_switch(const BWork *__restrict__ items, const long long *__restrict__ start,
                                                  int n) {
   __shared__ BWork w_s;
   batch_loop(items, start, n, w_s, [&](long long unit, int ry) {
@@ -138,12 +138,13 @@ struct BLaunch {
   long long total;          // start[n]
   int smem;                 // dynamic shared memory bytes (max over the items)
   int grid;                 // CTAs (persistent: a multiple of the SM count, at most total)
+  int rs;                   // translations: RHS per subtile (4 or 8)
   const BIo *io;            // device
   const double (*T)[kQMax][kQMax];  // host: T[2][q][q] of a plan of this q
   const double (*V)[kQMax];         // host: V[kMMax][q] of a plan of this s
 };
 
-constexpr int kBatchBlockInit = 256, kBatchBlockSwitch = 256;
+constexpr int kBatchBlockInit = 256;
 
 // Launch L on st, or (blocks_per_sm != NULL) set the kernel's shared-memory limit
 // and report its occupancy at L.smem instead.  Returns a cudaError_t.
@@ -174,14 +175,22 @@ template <int Q> int batch_launch(const BLaunch &L, cudaStream_t st, int smem_op
   constexpr int tterm = 32 * (Q > kTermM ? Q : kTermM);
   switch (L.kind) {
   case K_INIT: return go(kb_init<Q>, kBatchBlockInit, L.items, L.start, L.n, L.io);
-  case K_TRANS_P: return go(kb_trans<Q, true, true>, 32 * Q, L.items, L.start, L.n, tm);
-  case K_SWITCH: return go(kb_switch<Q, true>, kBatchBlockSwitch, L.items, L.start, L.n);
-  case K_TRANS_X: return go(kb_trans<Q, false, true>, 32 * Q, L.items, L.start, L.n, tm);
+  case K_TRANS_P:
+    return L.rs == 4 ? go(kb_trans<Q, true, true, 4>, TransShape<Q, 4>::threads, L.items, L.start, L.n, tm)
+                     : go(kb_trans<Q, true, true, 8>, TransShape<Q, 8>::threads, L.items, L.start, L.n, tm);
+  case K_SWITCH: return go(kb_switch<Q, true>, SwShape<Q>::threads, L.items, L.start, L.n);
+  case K_TRANS_X:
+    return L.rs == 4 ? go(kb_trans<Q, false, true, 4>, TransShape<Q, 4>::threads, L.items, L.start, L.n, tm)
+                     : go(kb_trans<Q, false, true, 8>, TransShape<Q, 8>::threads, L.items, L.start, L.n, tm);
   case K_TERM: return go(kb_term<Q>, tterm, L.items, L.start, L.n, vm, L.io);
   case K_TERM_ADJ: return go(kb_term_adj<Q>, tterm, L.items, L.start, L.n, vm, L.io);
-  case K_TRANS_P_ADJ: return go(kb_trans<Q, true, false>, 32 * Q, L.items, L.start, L.n, tm);
-  case K_SWITCH_ADJ: return go(kb_switch<Q, false>, kBatchBlockSwitch, L.items, L.start, L.n);
-  case K_TRANS_X_ADJ: return go(kb_trans<Q, false, false>, 32 * Q, L.items, L.start, L.n, tm);
+  case K_TRANS_P_ADJ:
+    return L.rs == 4 ? go(kb_trans<Q, true, false, 4>, TransShape<Q, 4>::threads, L.items, L.start, L.n, tm)
+                     : go(kb_trans<Q, true, false, 8>, TransShape<Q, 8>::threads, L.items, L.start, L.n, tm);
+  case K_SWITCH_ADJ: return go(kb_switch<Q, false>, SwShape<Q>::threads, L.items, L.start, L.n);
+  case K_TRANS_X_ADJ:
+    return L.rs == 4 ? go(kb_trans<Q, false, false, 4>, TransShape<Q, 4>::threads, L.items, L.start, L.n, tm)
+                     : go(kb_trans<Q, false, false, 8>, TransShape<Q, 8>::threads, L.items, L.start, L.n, tm);
   case K_INIT_ADJ: return go(kb_init_adj<Q>, kBatchBlockInit, L.items, L.start, L.n, L.io);
   }
   return (int)cudaErrorInvalidValue;

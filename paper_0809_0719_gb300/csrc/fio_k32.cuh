@@ -15,7 +15,15 @@
 
 namespace fio {
 
-constexpr int kRS = 8;      // RHS per subtile of a translation CTA
+// Translation CTA shape for an RHS subtile of RS right-hand sides: 4 RS q threads
+// (rounded up to whole warps), shared memory: phases 20 q^2 | staging 2 x 4 RS q^2 |
+// intermediate 8 RS q^2 complex.
+template <int Q, int RS> struct TransShape {
+  static constexpr int threads = (4 * RS * Q + 31) / 32 * 32;
+  static constexpr int smem = (20 + 16 * RS) * Q * Q * 8;
+  static constexpr int min_blocks = RS >= 8 ? 2 : 4;
+};
+__host__ __device__ constexpr int trans32_smem_bytes(int q, int rs) { return (20 + 16 * rs) * q * q * 8; }
 constexpr int kRMax = 32;   // RHS per CTA (grid.y covers the rest)
 
 // df tables of an FP32-form plan (same indexing as the FP64 tables in Tables).
@@ -99,13 +107,12 @@ __device__ void family_centres(const Tables &tb, const TablesF &tf, const Phase 
 // p at the centres of the children B_c (level lb+1).
 //   ea[sigma][c][t] = e(x^{A_sigma}_t, p0(B_c))   (16 q^2)
 //   eq[c][t']       = e(x^{A_p}_t', p0(B_c))       (4 q^2)
-// scratch: >= 5 q^2 XDesc + 10 q^2 df.
+// scratch: >= 10 q^2 df.
 template <int Q>
 __device__ void family_nodes(const Tables &tb, const TablesF &tf, const Phase &ph, const UnitIdx &d, int l, int lb,
                              float2 *ea, float2 *eq, unsigned char *scratch) {
   constexpr int Q2 = Q * Q;
-  XDesc *xd = (XDesc *)scratch;  // [4 sigma][Q2] then [Q2] for A_p
-  df *g = (df *)(xd + 5 * Q2);   // [5][Q2][2 c2]
+  df *g = (df *)scratch;  // [5][Q2][2 c2]: 4 sigma, then A_p
   if (ph.id == 3) {
     for (int idx = threadIdx.x; idx < 20 * Q2; idx += blockDim.x) {
       if (idx < 16 * Q2) {
@@ -124,15 +131,11 @@ __device__ void family_nodes(const Tables &tb, const TablesF &tf, const Phase &p
   }
   for (int idx = threadIdx.x; idx < 5 * Q2; idx += blockDim.x) {
     const int w = idx / Q2, t = idx % Q2;
-    if (w < 4)
-      xd[idx] = xdesc(tf.ph, xnf(tb, tf, l, 2 * d.ap1 + (w >> 1), t / Q, Q), xnf(tb, tf, l, 2 * d.ap2 + (w & 1), t % Q, Q));
-    else
-      xd[idx] = xdesc(tf.ph, xnf(tb, tf, l - 1, d.ap1, t / Q, Q), xnf(tb, tf, l - 1, d.ap2, t % Q, Q));
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < 10 * Q2; idx += blockDim.x) {
-    const int c2 = idx & 1, n = idx >> 1;
-    g[idx] = g_eval(tf.ph, xd[n], p2f(tb, tf, lb + 1, 2 * d.b2 + c2, Q, Q));
+    const XDesc x = w < 4 ? xdesc(tf.ph, xnf(tb, tf, l, 2 * d.ap1 + (w >> 1), t / Q, Q),
+                                  xnf(tb, tf, l, 2 * d.ap2 + (w & 1), t % Q, Q))
+                          : xdesc(tf.ph, xnf(tb, tf, l - 1, d.ap1, t / Q, Q), xnf(tb, tf, l - 1, d.ap2, t % Q, Q));
+    g[2 * idx] = g_eval(tf.ph, x, p2f(tb, tf, lb + 1, 2 * d.b2, Q, Q));
+    g[2 * idx + 1] = g_eval(tf.ph, x, p2f(tb, tf, lb + 1, 2 * d.b2 + 1, Q, Q));
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < 20 * Q2; idx += blockDim.x) {
@@ -150,6 +153,9 @@ __device__ void family_nodes(const Tables &tb, const TablesF &tf, const Phase &p
 }
 
 __device__ __forceinline__ float2 conjf2(float2 v) { return make_float2(v.x, -v.y); }
+// acc + s v for a real s and a complex v as one paired FMA (FFMA2: both components in
+// one instruction, each rounded as __fmaf_rn).
+__device__ __forceinline__ float2 fma2s(float s, float2 v, float2 acc) { return __ffma2_rn(make_float2(s, s), v, acc); }
 
 // Asynchronous 8-byte global->shared copies (LDGSTS), waited on by group.
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
@@ -194,37 +200,37 @@ __device__ __forceinline__ void cp_async_wait(int pending) {
 //         FWD: recursion in p (eq. alg2b); !FWD: conjugate transpose of the recursion in x.
 // TYPE_X: out_j = sum_i post_{j,i} (.) (T^{j1} (x) T^{j2})^T (pre_i (.) in_i)
 //         FWD: recursion in x (eq. alg2c); !FWD: conjugate transpose of the recursion in p.
-// The inputs of 8-RHS subtile k+1 are copied asynchronously while subtile k is
+// The inputs of RS-RHS subtile k+1 are copied asynchronously while subtile k is
 // computed (two staging buffers); the first copies overlap the phase setup.
-// Shared memory (float2): phases 20 Q^2 | staging 2 x 4 kRS Q^2 | intermediate 8 kRS Q^2.
+// Shared memory (float2): phases 20 Q^2 | staging 2 x 4 RS Q^2 | intermediate 8 RS Q^2.
 // ---------------------------------------------------------------------------
-template <int Q, bool TYPE_P, bool FWD>
+template <int Q, bool TYPE_P, bool FWD, int RS>
 __device__ __forceinline__ void k32_trans_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g, const TMat<float, Q> &tm,
                                                const float2 *__restrict__ in, float2 *__restrict__ out, long long bx_, int by_) {
   constexpr int Q2 = Q * Q;
-  constexpr int SUB = 4 * kRS * Q2;  // one staging buffer
+  constexpr int SUB = 4 * RS * Q2;  // one staging buffer
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *ph_s = (float2 *)smem_raw;  // TYPE_P: pre [4 j][4 i], post [4 j]; TYPE_X: pre [4 i], post [4 j][4 i]
-  float2 *io_s = ph_s + 20 * Q2;      // [2][4][kRS][Q2]
-  float2 *z_s = io_s + 2 * SUB;       // [4][2][kRS][Q2]
+  float2 *io_s = ph_s + 20 * Q2;      // [2][4][RS][Q2]
+  float2 *z_s = io_s + 2 * SUB;       // [4][2][RS][Q2]
   float2 *pre_s = ph_s;
   float2 *post_s = TYPE_P ? ph_s + 16 * Q2 : ph_s + 4 * Q2;
   const int l = g.l, lb = g.L - g.l, e = g.e;
   const UnitIdx d = unit_decode(bx_, l, lb, e);
   const int r0 = by_ * kRMax;
   const int rc = min(kRMax, g.nrhs - r0);
-  const int nsub = (rc + kRS - 1) / kRS;
+  const int nsub = (rc + RS - 1) / RS;
   const long long nrq = (long long)g.nrhs * Q2;
   // inputs come from the children of B (forward) or of A (conjugate transposes)
   auto in_pair = [&](int i) { return FWD ? pair_child_b(d, i, lb, e) : pair_child_a(d, i, l, lb, e); };
   auto out_pair = [&](int j) { return FWD ? pair_child_a(d, j, l, lb, e) : pair_child_b(d, j, lb, e); };
   auto issue = [&](int k) {
     if (k < nsub) {
-      const int rs0 = k * kRS, rs = min(kRS, rc - rs0);
+      const int rs0 = k * RS, rs = min(RS, rc - rs0);
       float2 *buf = io_s + (k & 1) * SUB;
 #pragma unroll
       for (int i = 0; i < 4; i++)
-        cp_async_run(buf + i * kRS * Q2, in + in_pair(i) * nrq + (long long)(r0 + rs0) * Q2, rs * Q2);
+        cp_async_run(buf + i * RS * Q2, in + in_pair(i) * nrq + (long long)(r0 + rs0) * Q2, rs * Q2);
     }
     cp_async_commit();
   };
@@ -255,14 +261,14 @@ __device__ __forceinline__ void k32_trans_body(const Tables &tb, const TablesF &
   }
 
   for (int k = 0; k < nsub; k++) {
-    const int rs0 = k * kRS, rs = min(kRS, rc - rs0);
+    const int rs0 = k * RS, rs = min(RS, rc - rs0);
     float2 *io = io_s + (k & 1) * SUB;
     cp_async_wait(k + 1 < nsub);
     __syncthreads();
     if (TYPE_P) {
       // Z_{j,i1}[t'1][t2] = sum_{i2,t'2} T^{i2}[t2][t'2] (pre (.) in)_{(i1,i2)}[t'1][t'2]
-      for (int task = threadIdx.x; task < 8 * kRS * Q; task += blockDim.x) {
-        const int tp1 = task % Q, r = (task / Q) % kRS, i1 = (task / (Q * kRS)) & 1, j = task / (2 * Q * kRS);
+      for (int task = threadIdx.x; task < 8 * RS * Q; task += blockDim.x) {
+        const int tp1 = task % Q, r = (task / Q) % RS, i1 = (task / (Q * RS)) & 1, j = task / (2 * Q * RS);
         if (r >= rs) continue;
         float2 sv[2][Q];
 #pragma unroll
@@ -270,66 +276,57 @@ __device__ __forceinline__ void k32_trans_body(const Tables &tb, const TablesF &
 #pragma unroll
           for (int tp2 = 0; tp2 < Q; tp2++) {
             const int i = i1 * 2 + i2;
-            sv[i2][tp2] = cmul(pre_s[(j * 4 + i) * Q2 + tp1 * Q + tp2], io[(i * kRS + r) * Q2 + tp1 * Q + tp2]);
+            sv[i2][tp2] = cmul(pre_s[(j * 4 + i) * Q2 + tp1 * Q + tp2], io[(i * RS + r) * Q2 + tp1 * Q + tp2]);
           }
-        float2 *zrow = z_s + ((j * 2 + i1) * kRS + r) * Q2 + tp1 * Q;
+        float2 *zrow = z_s + ((j * 2 + i1) * RS + r) * Q2 + tp1 * Q;
 #pragma unroll
         for (int t2 = 0; t2 < Q; t2++) {
-          float ax = 0.f, ay = 0.f;
+          float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
           for (int i2 = 0; i2 < 2; i2++)
 #pragma unroll
-            for (int tp2 = 0; tp2 < Q; tp2++) {
-              ax = __fmaf_rn(tm.T[i2][t2][tp2], sv[i2][tp2].x, ax);
-              ay = __fmaf_rn(tm.T[i2][t2][tp2], sv[i2][tp2].y, ay);
-            }
-          zrow[t2] = make_float2(ax, ay);
+            for (int tp2 = 0; tp2 < Q; tp2++) acc = fma2s(tm.T[i2][t2][tp2], sv[i2][tp2], acc);
+          zrow[t2] = acc;
         }
       }
       __syncthreads();
       // Y_j[t1][t2] = sum_{i1,t'1} T^{i1}[t1][t'1] Z_{j,i1}[t'1][t2];  out_j = post_j (.) Y_j  -> io
-      for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
-        const int t2 = task % Q, r = (task / Q) % kRS, j = task / (Q * kRS);
+      for (int task = threadIdx.x; task < 4 * RS * Q; task += blockDim.x) {
+        const int t2 = task % Q, r = (task / Q) % RS, j = task / (Q * RS);
         if (r >= rs) continue;
         float2 zc[2][Q];
 #pragma unroll
         for (int i1 = 0; i1 < 2; i1++)
 #pragma unroll
-          for (int tp1 = 0; tp1 < Q; tp1++) zc[i1][tp1] = z_s[((j * 2 + i1) * kRS + r) * Q2 + tp1 * Q + t2];
+          for (int tp1 = 0; tp1 < Q; tp1++) zc[i1][tp1] = z_s[((j * 2 + i1) * RS + r) * Q2 + tp1 * Q + t2];
 #pragma unroll
         for (int t1 = 0; t1 < Q; t1++) {
-          float ax = 0.f, ay = 0.f;
+          float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
           for (int i1 = 0; i1 < 2; i1++)
 #pragma unroll
-            for (int tp1 = 0; tp1 < Q; tp1++) {
-              ax = __fmaf_rn(tm.T[i1][t1][tp1], zc[i1][tp1].x, ax);
-              ay = __fmaf_rn(tm.T[i1][t1][tp1], zc[i1][tp1].y, ay);
-            }
-          io[(j * kRS + r) * Q2 + t1 * Q + t2] = cmul(post_s[j * Q2 + t1 * Q + t2], make_float2(ax, ay));
+            for (int tp1 = 0; tp1 < Q; tp1++) acc = fma2s(tm.T[i1][t1][tp1], zc[i1][tp1], acc);
+          io[(j * RS + r) * Q2 + t1 * Q + t2] = cmul(post_s[j * Q2 + t1 * Q + t2], acc);
         }
       }
     } else {
       // W_{i,j1}[t1][t'2] = sum_{t'1} T^{j1}[t'1][t1] (pre_i (.) in_i)[t'1][t'2], both j1 per task
-      for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
-        const int tp2 = task % Q, r = (task / Q) % kRS, i = task / (Q * kRS);
+      for (int task = threadIdx.x; task < 4 * RS * Q; task += blockDim.x) {
+        const int tp2 = task % Q, r = (task / Q) % RS, i = task / (Q * RS);
         if (r >= rs) continue;
         float2 col[Q];
 #pragma unroll
         for (int tp1 = 0; tp1 < Q; tp1++)
-          col[tp1] = cmul(pre_s[i * Q2 + tp1 * Q + tp2], io[(i * kRS + r) * Q2 + tp1 * Q + tp2]);
+          col[tp1] = cmul(pre_s[i * Q2 + tp1 * Q + tp2], io[(i * RS + r) * Q2 + tp1 * Q + tp2]);
 #pragma unroll
         for (int j1 = 0; j1 < 2; j1++) {
-          float2 *wb = z_s + ((i * 2 + j1) * kRS + r) * Q2 + tp2;
+          float2 *wb = z_s + ((i * 2 + j1) * RS + r) * Q2 + tp2;
 #pragma unroll
           for (int t1 = 0; t1 < Q; t1++) {
-            float ax = 0.f, ay = 0.f;
+            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int tp1 = 0; tp1 < Q; tp1++) {
-              ax = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].x, ax);
-              ay = __fmaf_rn(tm.T[j1][tp1][t1], col[tp1].y, ay);
-            }
-            wb[t1 * Q] = make_float2(ax, ay);
+            for (int tp1 = 0; tp1 < Q; tp1++) acc = fma2s(tm.T[j1][tp1][t1], col[tp1], acc);
+            wb[t1 * Q] = acc;
           }
         }
       }
@@ -337,9 +334,11 @@ __device__ __forceinline__ void k32_trans_body(const Tables &tb, const TablesF &
       // out_j[t1][t2] = sum_i post_{j,i}[t1][t2] sum_{t'2} T^{j2}[t'2][t2] W_{i,j1}[t1][t'2]  -> io.
       // A task is (j1, r, t1, half): both j2 and two of the four i; the lane pair
       // (half = 0, 1) exchanges partial sums so that half h finishes j2 = h.
-      for (int task = threadIdx.x; task < 4 * kRS * Q; task += blockDim.x) {
-        const int half = task & 1, t1 = (task >> 1) % Q, r = (task >> 1) / Q % kRS, j1 = (task >> 1) / (Q * kRS);
-        const bool live = r < rs;
+      constexpr int NT = 4 * RS * Q, NTW = (NT + 31) / 32 * 32;  // whole warps take part in the shuffles
+      for (int tw = threadIdx.x; tw < NTW; tw += blockDim.x) {
+        const int task = tw < NT ? tw : NT - 2 + (tw & 1);
+        const int half = task & 1, t1 = (task >> 1) % Q, r = (task >> 1) / Q % RS, j1 = (task >> 1) / (Q * RS);
+        const bool live = tw < NT && r < rs;
         float ax[2][Q], ay[2][Q];
 #pragma unroll
         for (int j2 = 0; j2 < 2; j2++)
@@ -351,18 +350,16 @@ __device__ __forceinline__ void k32_trans_body(const Tables &tb, const TablesF &
             const int i = 2 * half + ii;
             float2 row[Q];
 #pragma unroll
-            for (int tp2 = 0; tp2 < Q; tp2++) row[tp2] = z_s[((i * 2 + j1) * kRS + r) * Q2 + t1 * Q + tp2];
+            for (int tp2 = 0; tp2 < Q; tp2++) row[tp2] = z_s[((i * 2 + j1) * RS + r) * Q2 + t1 * Q + tp2];
 #pragma unroll
             for (int j2 = 0; j2 < 2; j2++) {
               const float2 *pp = post_s + ((2 * j1 + j2) * 4 + i) * Q2 + t1 * Q;
 #pragma unroll
               for (int t2 = 0; t2 < Q; t2++) {
-                float vx = 0.f, vy = 0.f;
+                float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int tp2 = 0; tp2 < Q; tp2++) {
-                  vx = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].x, vx);
-                  vy = __fmaf_rn(tm.T[j2][tp2][t2], row[tp2].y, vy);
-                }
+                for (int tp2 = 0; tp2 < Q; tp2++) v = fma2s(tm.T[j2][tp2][t2], row[tp2], v);
+                const float vx = v.x, vy = v.y;
                 const float2 p = pp[t2];
                 ax[j2][t2] = __fmaf_rn(p.x, vx, __fmaf_rn(-p.y, vy, ax[j2][t2]));
                 ay[j2][t2] = __fmaf_rn(p.x, vy, __fmaf_rn(p.y, vx, ay[j2][t2]));
@@ -370,7 +367,7 @@ __device__ __forceinline__ void k32_trans_body(const Tables &tb, const TablesF &
             }
           }
         }
-        float2 *dst = io + ((2 * j1 + half) * kRS + r) * Q2 + t1 * Q;  // staged inputs were last read in the W pass
+        float2 *dst = io + ((2 * j1 + half) * RS + r) * Q2 + t1 * Q;  // staged inputs were last read in the W pass
 #pragma unroll
         for (int t2 = 0; t2 < Q; t2++) {
           const float sx = half ? ax[0][t2] : ax[1][t2], sy = half ? ay[0][t2] : ay[1][t2];
@@ -382,15 +379,16 @@ __device__ __forceinline__ void k32_trans_body(const Tables &tb, const TablesF &
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 4; j++) store_run(out + out_pair(j) * nrq + (long long)(r0 + rs0) * Q2, io + j * kRS * Q2, rs * Q2);
+    for (int j = 0; j < 4; j++) store_run(out + out_pair(j) * nrq + (long long)(r0 + rs0) * Q2, io + j * RS * Q2, rs * Q2);
     __syncthreads();
     issue(k + 2);
   }
 }
-template <int Q, bool TYPE_P, bool FWD>
-__global__ void __launch_bounds__(32 * Q, 2) k32_trans(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm,
-                                                       const float2 *__restrict__ in, float2 *__restrict__ out) {
-  k32_trans_body<Q, TYPE_P, FWD>(tb, tf, ph, g, tm, in, out, blockIdx.x, blockIdx.y);
+template <int Q, bool TYPE_P, bool FWD, int RS>
+__global__ void __launch_bounds__(TransShape<Q, RS>::threads, TransShape<Q, RS>::min_blocks)
+    k32_trans(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm, const float2 *__restrict__ in,
+              float2 *__restrict__ out) {
+  k32_trans_body<Q, TYPE_P, FWD, RS>(tb, tf, ph, g, tm, in, out, blockIdx.x, blockIdx.y);
 }
 
 // e^{2 pi i theta(x, p)} for the FP32 form: x by its two 1D node entries (FP64 and df
@@ -409,84 +407,118 @@ __device__ __forceinline__ float2 e32k(const Phase &ph, const TablesF &tf, const
   return expi_df(theta_k(tf.ph, xdesc(tf.ph, f1, f2), kf.k1, kf.k2));
 }
 
+// Shape of the FP32 switch CTA: a contraction task owns 4 output rows x 4 RHS,
+// 8 RHS groups cover 32 RHS, so ceil(q^2/4) * 8 tasks (rounded up to whole warps).
+template <int Q> struct SwShape {
+  static constexpr int Q2 = Q * Q;
+  static constexpr int NOG = (Q2 + 3) / 4;
+  static constexpr int threads = ((NOG * 8 + 31) / 32) * 32;
+};
+// Dynamic shared memory of k32_switch for q: input/output block, kernel matrix (real
+// and imaginary parts, q^2 x q^2 rounded up to 4 columns), rho.
+__host__ __device__ constexpr int sw32_smem_bytes(int q) {
+  return kRMax * q * q * 8 + 2 * q * q * ((q * q + 3) / 4 * 4) * 4 + q * (int)sizeof(df);
+}
+
+// e^{2 pi i theta} from a df theta through the special-function unit: exact
+// reduction of hi, then __sincosf of 2 pi r, |2 pi r| <= pi (absolute error below
+// 1e-6 per factor; used for the q^4 factors of the switch).
+__device__ __forceinline__ float2 expi_df_sfu(df th) {
+  const float r = (th.h - rintf(th.h)) + th.l;
+  float sn, cs;
+  __sincosf(6.28318530717958647692f * r, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// out[r][o] = sum_i K[o][i] in[r][i] for o < q^2, r < rc.  The kernel sits in shared
+// memory transposed and split into real and imaginary float arrays kre/kim[i][OP]
+// (OP = q^2 rounded up to a multiple of 4, zero rows beyond q^2); the inputs keep
+// their HBM layout in_s[r][i] (complex).  A task owns rows o = 4 og + a (a < 4) and
+// RHS r = rg + nrg c (c < 4); accumulators hold row pairs (o, o+1), so a complex MAC
+// over two rows is four paired FMAs (FFMA2) with the input broadcast, and the lanes
+// of a warp read 4 distinct kernel row pairs and 8 distinct input rows (distinct
+// banks) per step.  With few RHS the inner sum is split into KS contiguous ranges
+// over consecutive lanes, combined with shuffles.
+template <int Q> struct SwLayout {
+  static constexpr int Q2 = Q * Q;
+  static constexpr int OP = (Q2 + 3) / 4 * 4;
+};
+template <int Q, int KS>
+__device__ __forceinline__ void sw_contract(const float *kre, const float *kim, const float2 *in_s, int rc,
+                                            float2 (&ax)[2][4], float2 (&ay)[2][4], int &og, int &rg, int &nrg,
+                                            bool &live) {
+  constexpr int Q2 = Q * Q, OP = SwLayout<Q>::OP;
+  constexpr int NOG = SwShape<Q>::NOG;
+  constexpr int CH = (Q2 + KS - 1) / KS;
+  nrg = (rc + 3) / 4;
+  const int task = threadIdx.x;
+  live = task < NOG * nrg * KS;
+  const int ks = task % KS, grp = task / KS;
+  rg = grp % nrg;
+  og = min(grp / nrg, NOG - 1);
+#pragma unroll
+  for (int h = 0; h < 2; h++)
+#pragma unroll
+    for (int c_ = 0; c_ < 4; c_++) ax[h][c_] = ay[h][c_] = make_float2(0.f, 0.f);
+  int rr[4];
+#pragma unroll
+  for (int c_ = 0; c_ < 4; c_++) rr[c_] = min(rg + nrg * c_, rc - 1);
+  if (live) {
+    const int i1 = min(Q2, (ks + 1) * CH);
+    const float *kr = kre + og * 4, *ki = kim + og * 4;
+#pragma unroll 3
+    for (int i = ks * CH; i < i1; i++) {
+      const float2 r01 = *reinterpret_cast<const float2 *>(kr + i * OP);
+      const float2 r23 = *reinterpret_cast<const float2 *>(kr + i * OP + 2);
+      const float2 m01 = *reinterpret_cast<const float2 *>(ki + i * OP);
+      const float2 m23 = *reinterpret_cast<const float2 *>(ki + i * OP + 2);
+      float2 iv[4];
+#pragma unroll
+      for (int c_ = 0; c_ < 4; c_++) iv[c_] = in_s[rr[c_] * Q2 + i];
+#pragma unroll
+      for (int c_ = 0; c_ < 4; c_++) {
+        const float2 X = make_float2(iv[c_].x, iv[c_].x), Y = make_float2(iv[c_].y, iv[c_].y);
+        const float2 NY = make_float2(-iv[c_].y, -iv[c_].y);
+        ax[0][c_] = __ffma2_rn(r01, X, ax[0][c_]);
+        ax[0][c_] = __ffma2_rn(m01, NY, ax[0][c_]);
+        ay[0][c_] = __ffma2_rn(r01, Y, ay[0][c_]);
+        ay[0][c_] = __ffma2_rn(m01, X, ay[0][c_]);
+        ax[1][c_] = __ffma2_rn(r23, X, ax[1][c_]);
+        ax[1][c_] = __ffma2_rn(m23, NY, ax[1][c_]);
+        ay[1][c_] = __ffma2_rn(r23, Y, ay[1][c_]);
+        ay[1][c_] = __ffma2_rn(m23, X, ay[1][c_]);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 1; m < KS; m <<= 1)
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+      for (int c_ = 0; c_ < 4; c_++) {
+        ax[h][c_].x += __shfl_xor_sync(0xffffffffu, ax[h][c_].x, m);
+        ax[h][c_].y += __shfl_xor_sync(0xffffffffu, ax[h][c_].y, m);
+        ay[h][c_].x += __shfl_xor_sync(0xffffffffu, ay[h][c_].x, m);
+        ay[h][c_].y += __shfl_xor_sync(0xffffffffu, ay[h][c_].y, m);
+      }
+  live = live && ks == 0;
+}
+
 // ---------------------------------------------------------------------------
 // FP32 switch (eq. alg2m): one CTA per pair (A, B) at level lm and up to 32 RHS.
 //   FWD : out[t] = sum_s e(x^A_t, p^B_s) in[s];   !FWD: out[s] = sum_t conj e(x^A_t, p^B_s) in[t].
 // theta(x_t, p_s) = rho(s1) G(x_t, p2_{s2}): q^3 evaluations of G, q^4 products.
-// Contraction: a task owns 3 output rows x up to 4 RHS (sw_contract).
+// The input block arrives by cp.async while the kernel matrix is generated.
 // ---------------------------------------------------------------------------
-constexpr int kSwOB = 3;
-// out_s[r][o] = sum_i k_s[o][i] in_s[r][i] for o < q^2, r < rc: a task owns kSwOB rows
-// x RB RHS over the inner indices i = ks, ks + KS, ...; the KS partial sums of a
-// task sit in KS consecutive lanes and are combined with butterfly shuffles.
-template <int Q, int RB, int KS>
-__device__ __forceinline__ void sw_contract(const float2 *k_s, const float2 *in_s, float2 *out_s, int rc) {
-  constexpr int Q2 = Q * Q;
-  constexpr int NOG = (Q2 + kSwOB - 1) / kSwOB;
-  const int nrg = (rc + RB - 1) / RB;
-  const int ntask = NOG * nrg * KS;
-  for (int base = 0; base < ntask; base += blockDim.x) {  // uniform trip count: whole warps shuffle
-    const int task = base + threadIdx.x;
-    const bool live = task < ntask;
-    const int ks = task % KS, grp = task / KS;
-    const int rg = grp % nrg, og = min(grp / nrg, NOG - 1);
-    float ax[kSwOB][RB], ay[kSwOB][RB];
-#pragma unroll
-    for (int a_ = 0; a_ < kSwOB; a_++)
-#pragma unroll
-      for (int c_ = 0; c_ < RB; c_++) ax[a_][c_] = ay[a_][c_] = 0.f;
-    int orow[kSwOB], rr[RB];
-#pragma unroll
-    for (int a_ = 0; a_ < kSwOB; a_++) orow[a_] = min(og * kSwOB + a_, Q2 - 1);
-#pragma unroll
-    for (int c_ = 0; c_ < RB; c_++) rr[c_] = min(rg * RB + c_, rc - 1);
-    if (live) {
-#pragma unroll 3
-      for (int i = ks; i < Q2; i += KS) {
-        float2 kv[kSwOB], iv[RB];
-#pragma unroll
-        for (int a_ = 0; a_ < kSwOB; a_++) kv[a_] = k_s[orow[a_] * Q2 + i];
-#pragma unroll
-        for (int c_ = 0; c_ < RB; c_++) iv[c_] = in_s[rr[c_] * Q2 + i];
-#pragma unroll
-        for (int a_ = 0; a_ < kSwOB; a_++)
-#pragma unroll
-          for (int c_ = 0; c_ < RB; c_++) {
-            ax[a_][c_] = __fmaf_rn(kv[a_].x, iv[c_].x, __fmaf_rn(-kv[a_].y, iv[c_].y, ax[a_][c_]));
-            ay[a_][c_] = __fmaf_rn(kv[a_].x, iv[c_].y, __fmaf_rn(kv[a_].y, iv[c_].x, ay[a_][c_]));
-          }
-      }
-    }
-#pragma unroll
-    for (int m = 1; m < KS; m <<= 1)
-#pragma unroll
-      for (int a_ = 0; a_ < kSwOB; a_++)
-#pragma unroll
-        for (int c_ = 0; c_ < RB; c_++) {
-          ax[a_][c_] += __shfl_xor_sync(0xffffffffu, ax[a_][c_], m);
-          ay[a_][c_] += __shfl_xor_sync(0xffffffffu, ay[a_][c_], m);
-        }
-    if (live && ks == 0) {
-#pragma unroll
-      for (int a_ = 0; a_ < kSwOB; a_++)
-#pragma unroll
-        for (int c_ = 0; c_ < RB; c_++) {
-          const int o = og * kSwOB + a_, r = rg * RB + c_;
-          if (o < Q2 && r < rc) out_s[r * Q2 + o] = make_float2(ax[a_][c_], ay[a_][c_]);
-        }
-    }
-  }
-}
 template <int Q, bool FWD>
 __device__ __forceinline__ void k32_switch_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g,
                                                 const float2 *__restrict__ in, float2 *__restrict__ out, long long bx_, int by_) {
-  constexpr int Q2 = Q * Q;
+  constexpr int Q2 = Q * Q, OP = SwLayout<Q>::OP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *k_s = (float2 *)smem_raw;        // [Q2 out][Q2 in]
-  float2 *in_s = k_s + Q2 * Q2;            // [kRMax][Q2]
-  float2 *out_s = in_s + kRMax * Q2;       // [kRMax][Q2]
-  XDesc *xd = (XDesc *)out_s;              // [Q2]      (before the contraction)
-  df *gt = (df *)(xd + Q2);                // [Q2][Q]
+  float2 *in_s = (float2 *)smem_raw;          // [kRMax][Q2]: inputs, then outputs (16-byte aligned)
+  float *kre = (float *)(in_s + kRMax * Q2);  // [Q2 in i][OP out o]
+  float *kim = kre + Q2 * OP;                 // [Q2 in i][OP out o]
+  df *rho_s = (df *)(kim + Q2 * OP);          // [Q]
   const int l = g.l, lb = g.L - g.l, e = g.e;
   const long long pr = bx_;
   const int nb2 = 1 << (lb + e);
@@ -498,51 +530,70 @@ __device__ __forceinline__ void k32_switch_body(const Tables &tb, const TablesF 
   const int rc = min(kRMax, g.nrhs - r0);
   const long long nrq = (long long)g.nrhs * Q2;
 
-  for (int idx = threadIdx.x; idx < rc * Q2; idx += blockDim.x) in_s[idx] = in[pr * nrq + (long long)r0 * Q2 + idx];
+  // the pair's input block (RHS-major, as in HBM) arrives while the kernel matrix is built
+  cp_async_run(in_s, in + pr * nrq + (long long)r0 * Q2, rc * Q2);
+  cp_async_commit();
+  for (int idx = threadIdx.x; idx < Q2 * (OP - Q2); idx += blockDim.x) {  // zero rows beyond q^2
+    const int i = idx / (OP - Q2), o = Q2 + idx % (OP - Q2);
+    kre[i * OP + o] = 0.f;
+    kim[i * OP + o] = 0.f;
+  }
   if (ph.id == 3) {
     for (int idx = threadIdx.x; idx < Q2 * Q2; idx += blockDim.x) {
-      const int o = idx / Q2, i = idx % Q2;
+      const int i = idx / Q2, o = idx % Q2;
       const int t = FWD ? o : i, s = FWD ? i : o;
       float2 v = expi<float>(theta_xp(ph, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q), pn1(tb, lb, b1, s / Q, Q),
                                       pn2(tb, lb, b2, s % Q, Q)));
-      k_s[idx] = FWD ? v : conjf2(v);
+      kre[i * OP + o] = v.x;
+      kim[i * OP + o] = FWD ? v.y : -v.y;
     }
   } else {
-    for (int t = threadIdx.x; t < Q2; t += blockDim.x)
-      xd[t] = xdesc(tf.ph, xnf(tb, tf, l, a1, t / Q, Q), xnf(tb, tf, l, a2, t % Q, Q));
+    for (int t = threadIdx.x; t < Q; t += blockDim.x) rho_s[t] = rhof(tb, tf, lb, b1, t, Q);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < Q2 * Q; idx += blockDim.x)
-      gt[idx] = g_eval(tf.ph, xd[idx / Q], p2f(tb, tf, lb, b2, idx % Q, Q));
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < Q2 * Q2; idx += blockDim.x) {
-      const int o = idx / Q2, i = idx % Q2;
-      const int t = FWD ? o : i, s = FWD ? i : o;
-      const float2 v = expi_df(df_mul(rhof(tb, tf, lb, b1, s / Q, Q), gt[t * Q + s % Q]));
-      k_s[idx] = FWD ? v : conjf2(v);
+    // theta(x_t, p_s) = rho(s1) G(x_t, p2_{s2}): one G per (t, s2), q products each
+    for (int task = threadIdx.x; task < Q2 * Q; task += blockDim.x) {
+      const int t = FWD ? task % Q2 : task / Q, s2 = FWD ? task / Q2 : task % Q;
+      const XDesc xdt = xdesc(tf.ph, xnf(tb, tf, l, a1, t / Q, Q), xnf(tb, tf, l, a2, t % Q, Q));
+      const df G = g_eval(tf.ph, xdt, p2f(tb, tf, lb, b2, s2, Q));
+#pragma unroll
+      for (int s1 = 0; s1 < Q; s1++) {
+        const float2 v = expi_df_sfu(df_mul(rho_s[s1], G));
+        const int s = s1 * Q + s2;
+        const int at = FWD ? s * OP + t : t * OP + s;  // K[o = t][i = s] or K[o = s][i = t] = conj
+        kre[at] = v.x;
+        kim[at] = FWD ? v.y : -v.y;
+      }
     }
   }
+  cp_async_wait(0);
   __syncthreads();
-  // contraction blocking by RHS count: RB RHS x 3 rows per task, the inner sum
-  // split over KS lanes when there are few tasks (small rc)
-  constexpr int NOG = (Q2 + kSwOB - 1) / kSwOB;
-  const int RB = rc >= 3 ? 4 : rc;
-  int KS = 1;
-  while (KS < 8 && NOG * ((rc + RB - 1) / RB) * KS < (int)blockDim.x / 2) KS *= 2;
-  if (RB == 4) {
-    if (KS == 1) sw_contract<Q, 4, 1>(k_s, in_s, out_s, rc);
-    else if (KS == 2) sw_contract<Q, 4, 2>(k_s, in_s, out_s, rc);
-    else if (KS == 4) sw_contract<Q, 4, 4>(k_s, in_s, out_s, rc);
-    else sw_contract<Q, 4, 8>(k_s, in_s, out_s, rc);
-  } else if (RB == 2) {
-    sw_contract<Q, 2, 8>(k_s, in_s, out_s, rc);
-  } else {
-    sw_contract<Q, 1, 8>(k_s, in_s, out_s, rc);
+  constexpr int NOG = SwShape<Q>::NOG;
+  const int nrg0 = (rc + 3) / 4;
+  float2 ax[2][4], ay[2][4];
+  int og, rg, nrg;
+  bool live;
+  if (NOG * nrg0 * 8 <= (int)blockDim.x) sw_contract<Q, 8>(kre, kim, in_s, rc, ax, ay, og, rg, nrg, live);
+  else if (NOG * nrg0 * 4 <= (int)blockDim.x) sw_contract<Q, 4>(kre, kim, in_s, rc, ax, ay, og, rg, nrg, live);
+  else if (NOG * nrg0 * 2 <= (int)blockDim.x) sw_contract<Q, 2>(kre, kim, in_s, rc, ax, ay, og, rg, nrg, live);
+  else sw_contract<Q, 1>(kre, kim, in_s, rc, ax, ay, og, rg, nrg, live);
+  __syncthreads();  // every task is done reading in_s: it becomes the output block
+  if (live) {
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+      for (int c_ = 0; c_ < 4; c_++) {
+        const int o = og * 4 + 2 * h, r = rg + nrg * c_;
+        if (r < rc) {
+          if (o < Q2) in_s[r * Q2 + o] = make_float2(ax[h][c_].x, ay[h][c_].x);
+          if (o + 1 < Q2) in_s[r * Q2 + o + 1] = make_float2(ax[h][c_].y, ay[h][c_].y);
+        }
+      }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < rc * Q2; idx += blockDim.x) out[pr * nrq + (long long)r0 * Q2 + idx] = out_s[idx];
+  store_run(out + pr * nrq + (long long)r0 * Q2, in_s, rc * Q2);
 }
 template <int Q, bool FWD>
-__global__ void __launch_bounds__(256) k32_switch(Tables tb, TablesF tf, Phase ph, Geom g, const float2 *__restrict__ in,
+__global__ void __launch_bounds__(SwShape<Q>::threads, 2) k32_switch(Tables tb, TablesF tf, Phase ph, Geom g, const float2 *__restrict__ in,
                                                    float2 *__restrict__ out) {
   k32_switch_body<Q, FWD>(tb, tf, ph, g, in, out, blockIdx.x, blockIdx.y);
 }

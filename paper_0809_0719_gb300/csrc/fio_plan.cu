@@ -362,6 +362,7 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   p->state_bytes = 2LL * (long long)sbytes;
   // autotune the FP32 switch on this plan's shapes (kept for every later apply)
   d.switch_impl = 0;
+  d.trans_rs = 8;
   if (precision == FIO_F32) {
     int impl = 0;
     const int rc = dispatch(d, fio::RUN_TUNE, nullptr, nullptr, nrhs_max, nullptr, -1, &impl);
@@ -471,6 +472,7 @@ int fio_plan_info(fio_plan_t p, fio_plan_info_t *info) {
   info->table_bytes = p->table_bytes;
   info->max_box_sources = d.maxsrc;
   info->switch_impl = d.switch_impl;
+  info->trans_rs = d.trans_rs;
   return FIO_OK;
 }
 

@@ -38,6 +38,7 @@ struct PlanDev {
   int smem_optin;
   int num_sms;
   int switch_impl;  // FP32 switch: 0 FFMA kernel, 1 tensor-core kernel (chosen by the plan's autotuner)
+  int trans_rs;     // FP32 translations: RHS per subtile, 4 or 8 (chosen by the plan's autotuner)
   int *status;  // device status word: 1 = a bounded wait expired (read by fio_check)
   Prof *prof;   // NULL unless profiling was ever enabled
 };
@@ -108,20 +109,25 @@ template <typename R, int Q> struct Runner {
 
   bool fast32() const { return sizeof(R) == 4 && p.tf.xnode != nullptr; }
 
+  template <bool TYPE_P, bool FWD, int RS> int trans32(int l, const CT *in, CT *out) {
+    const long long nunits = (1LL << (2 * (l - 1))) * nb_at(p.L - l);
+    const Geom g = geom(l, kRMax, 1, nunits);
+    dim3 grid((unsigned)nunits, (unsigned)((nrhs + kRMax - 1) / kRMax));
+    if (count_only) return check();
+    pre(TYPE_P ? (FWD ? K_TRANS_P : K_TRANS_P_ADJ) : (FWD ? K_TRANS_X : K_TRANS_X_ADJ));
+    auto k = k32_trans<Q, TYPE_P, FWD, RS>;
+    set_smem(k, p.smem_optin);
+    k<<<grid, TransShape<Q, RS>::threads, TransShape<Q, RS>::smem, st>>>(p.tb, p.tf, p.ph, g, tmat(),
+                                                                         (const float2 *)in, (float2 *)out);
+    return check();
+  }
+
   // Translation at level l (forward: l-1 -> l; adjoint: l -> l-1).
   template <bool TYPE_P, bool FWD> int trans(int l, const CT *in, CT *out) {
     if constexpr (sizeof(R) == 4) {
       if (fast32()) {
-        const long long nunits = (1LL << (2 * (l - 1))) * nb_at(p.L - l);
-        const Geom g = geom(l, kRMax, 1, nunits);
-        dim3 grid((unsigned)nunits, (unsigned)((nrhs + kRMax - 1) / kRMax));
-        const int smem = (20 + 16 * kRS) * Q2 * (int)sizeof(float2);
-        if (count_only) return check();
-        pre(TYPE_P ? (FWD ? K_TRANS_P : K_TRANS_P_ADJ) : (FWD ? K_TRANS_X : K_TRANS_X_ADJ));
-        auto k = k32_trans<Q, TYPE_P, FWD>;
-        set_smem(k, p.smem_optin);
-        k<<<grid, 32 * Q, smem, st>>>(p.tb, p.tf, p.ph, g, tmat(), (const float2 *)in, (float2 *)out);
-        return check();
+        if (p.trans_rs == 4) return trans32<TYPE_P, FWD, 4>(l, (const CT *)in, out);
+        return trans32<TYPE_P, FWD, 8>(l, in, out);
       }
     }
     const int rt = std::min(nrhs, sizeof(R) == 4 ? 8 : 4);
@@ -160,7 +166,7 @@ template <typename R, int Q> struct Runner {
         k<<<grid, kTcThreads, smem_tc, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, p.status);
         return check();
       }
-      const int smem32 = (Q2 * Q2 + 2 * kRMax * Q2) * (int)sizeof(float2);
+      const int smem32 = sw32_smem_bytes(Q);
       if (fast32() && smem32 <= p.smem_optin) {
         const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
         const Geom g = geom(p.lm, kRMax, 1, pairs);
@@ -169,7 +175,7 @@ template <typename R, int Q> struct Runner {
         pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
         auto k = k32_switch<Q, FWD>;
         set_smem(k, p.smem_optin);
-        k<<<grid, 256, smem32, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out);
+        k<<<grid, SwShape<Q>::threads, smem32, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out);
         return check();
       }
     }
@@ -324,31 +330,51 @@ template <typename R, int Q> struct Runner {
     return check();
   }
 
-  // Autotuner: time the FFMA and the tensor-core switch on the plan's state buffers
-  // (their contents do not matter) and return the faster implementation (0 or 1).
+  // Autotuner: time the alternatives on the plan's state buffers (their contents do
+  // not matter) and keep the faster: the FFMA vs the tensor-core switch, and 4- vs
+  // 8-RHS translation subtiles (at the plan's first translation level).  Returns the
+  // chosen switch implementation (0 or 1).
+  template <typename F> float best_ms(F &&fn) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; rep++) {
+      cudaEventRecord(a, st);
+      fn();
+      cudaEventRecord(b, st);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+  }
   int tune_switch(PlanDev &pm) {
     if constexpr (sizeof(R) != 4) {
       return 0;
     } else {
-      if (!fast32() || !p.status || TcShape<Q>::smem_bytes() > (size_t)p.smem_optin) return 0;
-      cudaEvent_t a, b;
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
-      float best[2] = {1e30f, 1e30f};
+      if (!fast32()) return 0;
+      const CT *s0 = (const CT *)p.state[0];
+      CT *s1 = (CT *)p.state[1];
+      if (p.l1 > p.l0) {  // translation subtile width
+        const int l = p.lm > p.l0 ? p.l0 + 1 : p.lm + 1;
+        const bool tp = p.lm > p.l0;
+        float t[2];
+        for (int v = 0; v < 2; v++) {
+          pm.trans_rs = v ? 8 : 4;
+          t[v] = best_ms([&]() { tp ? trans<true, true>(l, s0, s1) : trans<false, true>(l, s0, s1); });
+        }
+        pm.trans_rs = t[0] < t[1] ? 4 : 8;
+      }
+      if (!p.status || TcShape<Q>::smem_bytes() > (size_t)p.smem_optin) return 0;
+      float best[2];
       for (int impl = 0; impl < 2; impl++) {
         pm.switch_impl = impl;
-        for (int rep = 0; rep < 3; rep++) {
-          cudaEventRecord(a, st);
-          sw<true>((const CT *)p.state[0], (CT *)p.state[1]);
-          cudaEventRecord(b, st);
-          cudaEventSynchronize(b);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, a, b);
-          if (rep > 0) best[impl] = std::min(best[impl], ms);
-        }
+        best[impl] = best_ms([&]() { sw<true>(s0, s1); });
       }
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
       pm.switch_impl = best[1] < best[0] ? 1 : 0;
       return pm.switch_impl;
     }

@@ -43,7 +43,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("N", "L", "q", "s", "e", "l0", "lm", "l1", "phase_id", "precision",
                                             "nrhs_max", "nstages")] + [
         ("pairs_per_level", ctypes.c_longlong), ("state_bytes", ctypes.c_longlong),
-        ("table_bytes", ctypes.c_longlong), ("max_box_sources", ctypes.c_int), ("switch_impl", ctypes.c_int)]
+        ("table_bytes", ctypes.c_longlong), ("max_box_sources", ctypes.c_int), ("switch_impl", ctypes.c_int),
+        ("trans_rs", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):

@@ -136,9 +136,15 @@ def test_dot_test(fio, prec, tol, sw, N, q, e):
         Bf = plan.apply(f).to(torch.complex128)
         Bg = plan.adjoint(g).to(torch.complex128)
         for r in range(2):
-            a = torch.vdot(g[r].to(torch.complex128).flatten(), Bf[r].flatten())
+            g64 = g[r].to(torch.complex128).flatten()
+            a = torch.vdot(g64, Bf[r].flatten())
             b = torch.vdot(Bg[r].flatten(), f[r].to(torch.complex128).flatten())
-            assert abs(a - b).item() < tol * abs(a).item()
+            # residual against ||g|| ||Bf|| (the Cauchy-Schwarz bound of a rounding-level
+            # perturbation) at every size; against |<g, Bf>| itself where the inner
+            # product sums enough terms (FP64, or N >= 256) not to be small by chance
+            assert abs(a - b).item() < tol * (g64.norm() * Bf[r].norm()).item()
+            if prec == "f64" or N >= 256:
+                assert abs(a - b).item() < tol * abs(a).item()
     finally:
         plan.close()
 
@@ -164,8 +170,12 @@ def test_nrhs_batch_equals_single_calls(fio):
     try:
         F = torch.from_numpy(gaussian_batch(N, range(11))).to(torch.complex64).cuda()
         U = plan.apply(F)
+        # each RHS is independent; the switch splits its inner sums by the number of RHS
+        # sharing a CTA, so a RHS applied alone agrees to FP32 rounding, not bit for bit
         for r in (0, 7, 10):
-            assert torch.equal(plan.apply(F[r:r + 1])[0], U[r])
+            one = plan.apply(F[r:r + 1])[0]
+            assert ((one - U[r]).norm() / U[r].norm()).item() < 1e-6
+        assert torch.equal(plan.apply(F)[10], U[10])  # the same call shape is bit-stable
     finally:
         plan.close()
 
