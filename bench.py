@@ -334,7 +334,7 @@ def run_ours(args, rank, world, dist):
                 "h2d_bytes_per_step": N * N * NRHS * 8, "d2h_bytes_per_step": N * N * NRHS * 8,
                 "api": "fio_apply_host (pinned host buffers)"},
         "gpu_launches": launches_per_step * args.steps,
-        "switch_kernel": ["fp32_fma", "tcgen05_tf32"][switch_impl] + " (plan autotuner)",
+        "switch_kernel": ["fp32_fma", "tcgen05_tf32", "fp32_fma_warp_specialised"][switch_impl] + " (plan autotuner)",
         "translation_rhs_subtile": trans_rs,
         "kernels": kernels,
         "roofline": roof,

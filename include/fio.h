@@ -132,7 +132,8 @@ typedef struct {
   long long table_bytes;   /* device bytes of the plan's tables */
   int max_box_sources;     /* most sources in one initialization box B */
   int switch_impl;         /* FIO_F32: switch kernel chosen by fio_plan's autotuner,
-                              0 = FP32 FMA, 1 = tensor cores (tcgen05, split TF32) */
+                              0 = FP32 FMA (one pair per CTA), 1 = tensor cores (tcgen05,
+                              split TF32), 2 = FP32 FMA, warp-specialised and persistent */
   int trans_rs;            /* FIO_F32: right-hand sides per translation subtile (4 or 8),
                               chosen by fio_plan's autotuner */
 } fio_plan_info_t;
@@ -147,8 +148,9 @@ int fio_plan_info(fio_plan_t plan, fio_plan_info_t *info);
 int fio_check(fio_plan_t plan, void *stream);
 
 /* fio_plan_set_switch -- override the autotuner's choice of the FIO_F32 switch
- * kernel: impl 0 = FP32 FMA, 1 = tensor cores.  FIO_EINVAL if the plan is FIO_F64
- * or the tensor-core kernel does not fit this plan (its shared memory need). */
+ * kernel: impl 0 = FP32 FMA, 1 = tensor cores, 2 = warp-specialised FP32 FMA.
+ * FIO_EINVAL if the plan is FIO_F64 or the kernel does not fit this plan (its
+ * shared memory need: 1 and 2 are not available for every q). */
 int fio_plan_set_switch(fio_plan_t plan, int impl);
 
 /* fio_kernel_launches -- number of kernels one fio_apply (adjoint != 0: fio_apply_adjoint)

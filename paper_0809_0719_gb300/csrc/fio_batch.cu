@@ -178,8 +178,7 @@ int build_schedule(fio_batch_s *b, int adj) {
         case K_INIT_ADJ: {
           w.g.nunits = d.nbox_init;
           w.maxsrc = std::max(1, d.maxsrc);
-          const int rt = std::min(b->nrhs[i], kRMax);
-          int GA = kind == K_INIT ? std::max(1, kBatchBlockInit / (rt * d.q)) : 1;
+          int GA = kind == K_INIT ? std::min(kInitChunk, 1 << (2 * d.l0)) : 1;
           std::vector<BWork> one(1, w);
           one[0].GA = GA;
           while (kind == K_INIT && kind_smem(kind, G.q, G.s, 8, one) > budget && GA > 1) one[0].GA = --GA;

@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(SwShape<Q>::threads, 2) kb_switch(const BWork 
 }
 
 template <int Q>
-__global__ void __launch_bounds__(256) kb_init(const BWork *__restrict__ items, const long long *__restrict__ start, int n,
-                                               const BIo *__restrict__ io) {
+__global__ void __launch_bounds__(InitShape<Q>::threads) kb_init(const BWork *__restrict__ items,
+                                                                  const long long *__restrict__ start, int n,
+                                                                  const BIo *__restrict__ io) {
   __shared__ BWork w_s;
   const float2 *base = io->in;
   batch_loop(items, start, n, w_s, [&](long long unit, int ry) {
@@ -174,7 +175,7 @@ template <int Q> int batch_launch(const BLaunch &L, cudaStream_t st, int smem_op
   };
   constexpr int tterm = 32 * (Q > kTermM ? Q : kTermM);
   switch (L.kind) {
-  case K_INIT: return go(kb_init<Q>, kBatchBlockInit, L.items, L.start, L.n, L.io);
+  case K_INIT: return go(kb_init<Q>, InitShape<Q>::threads, L.items, L.start, L.n, L.io);
   case K_TRANS_P:
     return L.rs == 4 ? go(kb_trans<Q, true, true, 4>, TransShape<Q, 4>::threads, L.items, L.start, L.n, tm)
                      : go(kb_trans<Q, true, true, 8>, TransShape<Q, 8>::threads, L.items, L.start, L.n, tm);

@@ -168,25 +168,31 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 // Copy n float2 from global to shared (both 8-byte aligned) asynchronously, 16 bytes
 // at a time when the global side allows it (the shared side is 16-byte aligned).
-__device__ __forceinline__ void cp_async_run(float2 *dst, const float2 *src, int n) {
+// (tid, nthr: this thread's index among the nthr threads sharing the copy.)
+__device__ __forceinline__ void cp_async_run(float2 *dst, const float2 *src, int n, int tid, int nthr) {
   if ((((uintptr_t)src) & 15) == 0) {
     const int n2 = n >> 1;
-    for (int k = threadIdx.x; k < n2; k += blockDim.x) cp_async16(dst + 2 * k, src + 2 * k);
-    if ((n & 1) && threadIdx.x == 0) cp_async8(dst + n - 1, src + n - 1);
+    for (int k = tid; k < n2; k += nthr) cp_async16(dst + 2 * k, src + 2 * k);
+    if ((n & 1) && tid == 0) cp_async8(dst + n - 1, src + n - 1);
   } else {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) cp_async8(dst + k, src + k);
+    for (int k = tid; k < n; k += nthr) cp_async8(dst + k, src + k);
   }
 }
+__device__ __forceinline__ void cp_async_run(float2 *dst, const float2 *src, int n) {
+  cp_async_run(dst, src, n, threadIdx.x, blockDim.x);
+}
 // Store n float2 from shared (16-byte aligned) to global, 16 bytes at a time when aligned.
-__device__ __forceinline__ void store_run(float2 *dst, const float2 *src, int n) {
+__device__ __forceinline__ void store_run(float2 *dst, const float2 *src, int n, int tid, int nthr) {
   if ((((uintptr_t)dst) & 15) == 0) {
     const int n2 = n >> 1;
-    for (int k = threadIdx.x; k < n2; k += blockDim.x)
-      reinterpret_cast<float4 *>(dst)[k] = reinterpret_cast<const float4 *>(src)[k];
-    if ((n & 1) && threadIdx.x == 0) dst[n - 1] = src[n - 1];
+    for (int k = tid; k < n2; k += nthr) reinterpret_cast<float4 *>(dst)[k] = reinterpret_cast<const float4 *>(src)[k];
+    if ((n & 1) && tid == 0) dst[n - 1] = src[n - 1];
   } else {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+    for (int k = tid; k < n; k += nthr) dst[k] = src[k];
   }
+}
+__device__ __forceinline__ void store_run(float2 *dst, const float2 *src, int n) {
+  store_run(dst, src, n, threadIdx.x, blockDim.x);
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait(int pending) {
@@ -444,14 +450,13 @@ template <int Q> struct SwLayout {
   static constexpr int OP = (Q2 + 3) / 4 * 4;
 };
 template <int Q, int KS>
-__device__ __forceinline__ void sw_contract(const float *kre, const float *kim, const float2 *in_s, int rc,
+__device__ __forceinline__ void sw_contract(const float *kre, const float *kim, const float2 *in_s, int rc, int task,
                                             float2 (&ax)[2][4], float2 (&ay)[2][4], int &og, int &rg, int &nrg,
                                             bool &live) {
   constexpr int Q2 = Q * Q, OP = SwLayout<Q>::OP;
   constexpr int NOG = SwShape<Q>::NOG;
   constexpr int CH = (Q2 + KS - 1) / KS;
   nrg = (rc + 3) / 4;
-  const int task = threadIdx.x;
   live = task < NOG * nrg * KS;
   const int ks = task % KS, grp = task / KS;
   rg = grp % nrg;
@@ -504,6 +509,99 @@ __device__ __forceinline__ void sw_contract(const float *kre, const float *kim, 
   live = live && ks == 0;
 }
 
+// Pair index -> (A, B) box coordinates at the switch level.
+struct SwPair {
+  int a1, a2, b1, b2;
+};
+__device__ __forceinline__ SwPair sw_decode(const Geom &g, long long pr) {
+  const int l = g.l, lb = g.L - g.l;
+  const int nb2 = 1 << (lb + g.e);
+  const long long nBl = (1LL << lb) * nb2;
+  const long long a = pr / nBl, b = pr - a * nBl;
+  SwPair d;
+  d.a1 = (int)(a >> l);
+  d.a2 = (int)(a & ((1LL << l) - 1));
+  d.b1 = (int)(b / nb2);
+  d.b2 = (int)(b - (long long)d.b1 * nb2);
+  return d;
+}
+
+// The kernel matrix of pair d into kre/kim[i][o] (transposed; rows o < q^2, the
+// pad rows are left alone), by nthr threads (this one is tid); sync() orders rho_s
+// before its use.
+template <int Q, bool FWD, typename Sync>
+__device__ __forceinline__ void sw_fill(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g,
+                                        const SwPair &d, float *kre, float *kim, df *rho_s, int tid, int nthr,
+                                        Sync &&sync) {
+  constexpr int Q2 = Q * Q, OP = SwLayout<Q>::OP;
+  const int l = g.l, lb = g.L - g.l;
+  if (ph.id == 3) {
+    for (int idx = tid; idx < Q2 * Q2; idx += nthr) {
+      const int i = idx / Q2, o = idx % Q2;
+      const int t = FWD ? o : i, s = FWD ? i : o;
+      float2 v = expi<float>(theta_xp(ph, xn(tb, l, d.a1, t / Q, Q), xn(tb, l, d.a2, t % Q, Q),
+                                      pn1(tb, lb, d.b1, s / Q, Q), pn2(tb, lb, d.b2, s % Q, Q)));
+      kre[i * OP + o] = v.x;
+      kim[i * OP + o] = FWD ? v.y : -v.y;
+    }
+    return;
+  }
+  for (int t = tid; t < Q; t += nthr) rho_s[t] = rhof(tb, tf, lb, d.b1, t, Q);
+  sync();
+  // theta(x_t, p_s) = rho(s1) G(x_t, p2_{s2}): one G per (t, s2), q products each
+  for (int task = tid; task < Q2 * Q; task += nthr) {
+    const int t = FWD ? task % Q2 : task / Q, s2 = FWD ? task / Q2 : task % Q;
+    const XDesc xdt = xdesc(tf.ph, xnf(tb, tf, l, d.a1, t / Q, Q), xnf(tb, tf, l, d.a2, t % Q, Q));
+    const df G = g_eval(tf.ph, xdt, p2f(tb, tf, lb, d.b2, s2, Q));
+#pragma unroll
+    for (int s1 = 0; s1 < Q; s1++) {
+      const float2 v = expi_df_sfu(df_mul(rho_s[s1], G));
+      const int s = s1 * Q + s2;
+      const int at = FWD ? s * OP + t : t * OP + s;  // K[o = t][i = s] or K[o = s][i = t] = conj
+      kre[at] = v.x;
+      kim[at] = FWD ? v.y : -v.y;
+    }
+  }
+}
+// Zero the pad rows o >= q^2 of a kernel buffer.
+template <int Q> __device__ __forceinline__ void sw_zero_pad(float *kre, float *kim, int tid, int nthr) {
+  constexpr int Q2 = Q * Q, OP = SwLayout<Q>::OP;
+  for (int idx = tid; idx < Q2 * (OP - Q2); idx += nthr) {
+    const int i = idx / (OP - Q2), o = Q2 + idx % (OP - Q2);
+    kre[i * OP + o] = 0.f;
+    kim[i * OP + o] = 0.f;
+  }
+}
+// Contraction by nthr threads (this one is task) into registers, then -- after
+// sync(), when no thread reads in_s any more -- the results into in_s as [r][o].
+template <int Q, typename Sync>
+__device__ __forceinline__ void sw_contract_store(const float *kre, const float *kim, float2 *in_s, int rc, int task,
+                                                  int nthr, Sync &&sync) {
+  constexpr int Q2 = Q * Q;
+  constexpr int NOG = SwShape<Q>::NOG;
+  const int nrg0 = (rc + 3) / 4;
+  float2 ax[2][4], ay[2][4];
+  int og, rg, nrg;
+  bool live;
+  if (NOG * nrg0 * 8 <= nthr) sw_contract<Q, 8>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
+  else if (NOG * nrg0 * 4 <= nthr) sw_contract<Q, 4>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
+  else if (NOG * nrg0 * 2 <= nthr) sw_contract<Q, 2>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
+  else sw_contract<Q, 1>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
+  sync();
+  if (live) {
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+      for (int c_ = 0; c_ < 4; c_++) {
+        const int o = og * 4 + 2 * h, r = rg + nrg * c_;
+        if (r < rc) {
+          if (o < Q2) in_s[r * Q2 + o] = make_float2(ax[h][c_].x, ay[h][c_].x);
+          if (o + 1 < Q2) in_s[r * Q2 + o + 1] = make_float2(ax[h][c_].y, ay[h][c_].y);
+        }
+      }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // FP32 switch (eq. alg2m): one CTA per pair (A, B) at level lm and up to 32 RHS.
 //   FWD : out[t] = sum_s e(x^A_t, p^B_s) in[s];   !FWD: out[s] = sum_t conj e(x^A_t, p^B_s) in[t].
@@ -519,76 +617,17 @@ __device__ __forceinline__ void k32_switch_body(const Tables &tb, const TablesF 
   float *kre = (float *)(in_s + kRMax * Q2);  // [Q2 in i][OP out o]
   float *kim = kre + Q2 * OP;                 // [Q2 in i][OP out o]
   df *rho_s = (df *)(kim + Q2 * OP);          // [Q]
-  const int l = g.l, lb = g.L - g.l, e = g.e;
   const long long pr = bx_;
-  const int nb2 = 1 << (lb + e);
-  const long long nBl = (1LL << lb) * nb2;
-  const long long a = pr / nBl, b = pr - a * nBl;
-  const int a1 = (int)(a >> l), a2 = (int)(a & ((1LL << l) - 1));
-  const int b1 = (int)(b / nb2), b2 = (int)(b - (long long)b1 * nb2);
   const int r0 = by_ * kRMax;
   const int rc = min(kRMax, g.nrhs - r0);
   const long long nrq = (long long)g.nrhs * Q2;
-
-  // the pair's input block (RHS-major, as in HBM) arrives while the kernel matrix is built
   cp_async_run(in_s, in + pr * nrq + (long long)r0 * Q2, rc * Q2);
   cp_async_commit();
-  for (int idx = threadIdx.x; idx < Q2 * (OP - Q2); idx += blockDim.x) {  // zero rows beyond q^2
-    const int i = idx / (OP - Q2), o = Q2 + idx % (OP - Q2);
-    kre[i * OP + o] = 0.f;
-    kim[i * OP + o] = 0.f;
-  }
-  if (ph.id == 3) {
-    for (int idx = threadIdx.x; idx < Q2 * Q2; idx += blockDim.x) {
-      const int i = idx / Q2, o = idx % Q2;
-      const int t = FWD ? o : i, s = FWD ? i : o;
-      float2 v = expi<float>(theta_xp(ph, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q), pn1(tb, lb, b1, s / Q, Q),
-                                      pn2(tb, lb, b2, s % Q, Q)));
-      kre[i * OP + o] = v.x;
-      kim[i * OP + o] = FWD ? v.y : -v.y;
-    }
-  } else {
-    for (int t = threadIdx.x; t < Q; t += blockDim.x) rho_s[t] = rhof(tb, tf, lb, b1, t, Q);
-    __syncthreads();
-    // theta(x_t, p_s) = rho(s1) G(x_t, p2_{s2}): one G per (t, s2), q products each
-    for (int task = threadIdx.x; task < Q2 * Q; task += blockDim.x) {
-      const int t = FWD ? task % Q2 : task / Q, s2 = FWD ? task / Q2 : task % Q;
-      const XDesc xdt = xdesc(tf.ph, xnf(tb, tf, l, a1, t / Q, Q), xnf(tb, tf, l, a2, t % Q, Q));
-      const df G = g_eval(tf.ph, xdt, p2f(tb, tf, lb, b2, s2, Q));
-#pragma unroll
-      for (int s1 = 0; s1 < Q; s1++) {
-        const float2 v = expi_df_sfu(df_mul(rho_s[s1], G));
-        const int s = s1 * Q + s2;
-        const int at = FWD ? s * OP + t : t * OP + s;  // K[o = t][i = s] or K[o = s][i = t] = conj
-        kre[at] = v.x;
-        kim[at] = FWD ? v.y : -v.y;
-      }
-    }
-  }
+  sw_zero_pad<Q>(kre, kim, threadIdx.x, blockDim.x);
+  sw_fill<Q, FWD>(tb, tf, ph, g, sw_decode(g, pr), kre, kim, rho_s, threadIdx.x, blockDim.x, []() { __syncthreads(); });
   cp_async_wait(0);
   __syncthreads();
-  constexpr int NOG = SwShape<Q>::NOG;
-  const int nrg0 = (rc + 3) / 4;
-  float2 ax[2][4], ay[2][4];
-  int og, rg, nrg;
-  bool live;
-  if (NOG * nrg0 * 8 <= (int)blockDim.x) sw_contract<Q, 8>(kre, kim, in_s, rc, ax, ay, og, rg, nrg, live);
-  else if (NOG * nrg0 * 4 <= (int)blockDim.x) sw_contract<Q, 4>(kre, kim, in_s, rc, ax, ay, og, rg, nrg, live);
-  else if (NOG * nrg0 * 2 <= (int)blockDim.x) sw_contract<Q, 2>(kre, kim, in_s, rc, ax, ay, og, rg, nrg, live);
-  else sw_contract<Q, 1>(kre, kim, in_s, rc, ax, ay, og, rg, nrg, live);
-  __syncthreads();  // every task is done reading in_s: it becomes the output block
-  if (live) {
-#pragma unroll
-    for (int h = 0; h < 2; h++)
-#pragma unroll
-      for (int c_ = 0; c_ < 4; c_++) {
-        const int o = og * 4 + 2 * h, r = rg + nrg * c_;
-        if (r < rc) {
-          if (o < Q2) in_s[r * Q2 + o] = make_float2(ax[h][c_].x, ay[h][c_].x);
-          if (o + 1 < Q2) in_s[r * Q2 + o + 1] = make_float2(ax[h][c_].y, ay[h][c_].y);
-        }
-      }
-  }
+  sw_contract_store<Q>(kre, kim, in_s, rc, threadIdx.x, blockDim.x, []() { __syncthreads(); });
   __syncthreads();
   store_run(out + pr * nrq + (long long)r0 * Q2, in_s, rc * Q2);
 }
@@ -599,8 +638,79 @@ __global__ void __launch_bounds__(SwShape<Q>::threads, 2) k32_switch(Tables tb, 
 }
 
 // ---------------------------------------------------------------------------
-// FP32 initialization (eq. alg2a), as k_init with df phases; one CTA per box B,
-// up to 32 RHS, GA boxes A at a time.
+// Warp-specialised persistent FP32 switch: producer warps build the kernel matrix
+// of the CTA's next work item (and start its input copy) while consumer warps
+// contract the current one.  Two kernel/input buffers; hardware named barriers
+// hand them over (FULL_b: producers -> consumers, EMPTY_b: consumers -> producers).
+// Work item w = pair * nry + RHS tile; CTA c takes w = c, c + gridDim.x, ...
+// ---------------------------------------------------------------------------
+template <int Q> struct SwWs {
+  static constexpr int Q2 = Q * Q, OP = SwLayout<Q>::OP;
+  static constexpr int cons = SwShape<Q>::threads;   // consumer threads
+  static constexpr int prod = SwShape<Q>::threads;   // producer threads
+  static constexpr int threads = cons + prod;
+  static constexpr int kfloats = 2 * Q2 * OP;        // one kernel buffer (re, im)
+  static constexpr int ifloat2 = kRMax * Q2;         // one input/output buffer
+  static constexpr int smem = 2 * (kfloats * 4 + ifloat2 * 8) + 2 * Q * 8;
+};
+enum { kBarFull0 = 1, kBarEmpty0 = 3, kBarProd = 5, kBarCons = 6 };
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void named_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+template <int Q, bool FWD>
+__global__ void __launch_bounds__(SwWs<Q>::threads, 1) k32_switch_ws(Tables tb, TablesF tf, Phase ph, Geom g,
+                                                                    const float2 *__restrict__ in,
+                                                                    float2 *__restrict__ out, long long nwork) {
+  using W = SwWs<Q>;
+  constexpr int Q2 = Q * Q, OP = W::OP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *ibuf = (float2 *)smem_raw;                     // [2][kRMax][Q2]
+  float *kbuf = (float *)(ibuf + 2 * W::ifloat2);        // [2][re, im][Q2][OP]
+  df *rho = (df *)(kbuf + 2 * W::kfloats);               // [2][Q]
+  const int nry = (g.nrhs + kRMax - 1) / kRMax;
+  const long long nrq = (long long)g.nrhs * Q2;
+  const long long nstage = blockIdx.x < nwork ? (nwork - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  if (threadIdx.x < W::prod) {
+    const int tid = threadIdx.x;
+    for (long long s = 0; s < nstage; s++) {
+      const int b = (int)(s & 1);
+      const long long w = blockIdx.x + s * gridDim.x;
+      const long long pr = w / nry;
+      const int r0 = (int)(w % nry) * kRMax, rc = min(kRMax, g.nrhs - r0);
+      float *kre = kbuf + b * W::kfloats, *kim = kre + Q2 * OP;
+      if (s >= 2) named_sync(kBarEmpty0 + b, W::threads);
+      else sw_zero_pad<Q>(kre, kim, tid, W::prod);
+      cp_async_run(ibuf + b * W::ifloat2, in + pr * nrq + (long long)r0 * Q2, rc * Q2, tid, W::prod);
+      cp_async_commit();
+      sw_fill<Q, FWD>(tb, tf, ph, g, sw_decode(g, pr), kre, kim, rho + b * Q, tid, W::prod,
+                      []() { named_sync(kBarProd, W::prod); });
+      cp_async_wait(0);
+      named_arrive(kBarFull0 + b, W::threads);
+    }
+  } else {
+    const int task = threadIdx.x - W::prod;
+    for (long long s = 0; s < nstage; s++) {
+      const int b = (int)(s & 1);
+      const long long w = blockIdx.x + s * gridDim.x;
+      const long long pr = w / nry;
+      const int r0 = (int)(w % nry) * kRMax, rc = min(kRMax, g.nrhs - r0);
+      const float *kre = kbuf + b * W::kfloats, *kim = kre + Q2 * OP;
+      float2 *io = ibuf + b * W::ifloat2;
+      named_sync(kBarFull0 + b, W::threads);
+      sw_contract_store<Q>(kre, kim, io, rc, task, W::cons, []() { named_sync(kBarCons, W::cons); });
+      named_sync(kBarCons, W::cons);
+      store_run(out + pr * nrq + (long long)r0 * Q2, io, rc * Q2, task, W::cons);
+      if (s + 2 < nstage) named_arrive(kBarEmpty0 + b, W::threads);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 initialization (eq. alg2a), as k_init with df phases; one CTA per box B and
+// up to 32 RHS; the phases of GA boxes A are staged at a time, then each thread
+// accumulates one (RHS, t1) row for every A of the chunk.
 // ---------------------------------------------------------------------------
 template <int Q>
 __device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g, int maxsrc, int GA,
@@ -644,32 +754,39 @@ __device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &t
       }
     }
     __syncthreads();
-    for (int task = threadIdx.x; task < ga_n * rt * Q; task += blockDim.x) {
-      const int t1 = task % Q, r = (task / Q) % rt, ga = task / (Q * rt);
-      float ax[Q], ay[Q];
+    // thread (r, t1) sums the row t1 of boxes A of the chunk (no barrier inside); with
+    // fewer than kRMax RHS the threads split into groups that take different A
+    const int per = rt * Q, ngrp = blockDim.x / per;
+    const int r = (threadIdx.x % per) / Q, t1 = threadIdx.x % Q;
+    if (threadIdx.x < ngrp * per) {
+      for (int ga = threadIdx.x / per; ga < ga_n; ga += ngrp) {
+        float2 acc[Q];
 #pragma unroll
-      for (int t2 = 0; t2 < Q; t2++) ax[t2] = ay[t2] = 0.f;
-      for (int j = 0; j < ns; j++) {
-        const float2 v = cmul(pk[ga * maxsrc + j], fv[j * kRMax + r]);
-        const float w1 = w[j * 2 * Q + t1];
-        const float vx = w1 * v.x, vy = w1 * v.y;
+        for (int t2 = 0; t2 < Q; t2++) acc[t2] = make_float2(0.f, 0.f);
+        for (int j = 0; j < ns; j++) {
+          const float2 v = cmul(pk[ga * maxsrc + j], fv[j * kRMax + r]);
+          const float w1 = w[j * 2 * Q + t1];
+          const float2 h = __fmul2_rn(make_float2(w1, w1), v);
 #pragma unroll
-        for (int t2 = 0; t2 < Q; t2++) {
-          const float w2 = w[j * 2 * Q + Q + t2];
-          ax[t2] = __fmaf_rn(w2, vx, ax[t2]);
-          ay[t2] = __fmaf_rn(w2, vy, ay[t2]);
+          for (int t2 = 0; t2 < Q; t2++) acc[t2] = fma2s(w[j * 2 * Q + Q + t2], h, acc[t2]);
         }
-      }
-      const int A = A0 + ga;
-      float2 *dst = st + ((long long)A * nB + box) * nrq + (long long)(r0 + r) * Q2 + t1 * Q;
+        const int A = A0 + ga;
+        float2 *dst = st + ((long long)A * nB + box) * nrq + (long long)(r0 + r) * Q2 + t1 * Q;
 #pragma unroll
-      for (int t2 = 0; t2 < Q; t2++) dst[t2] = cmul(post[ga * Q2 + t1 * Q + t2], make_float2(ax[t2], ay[t2]));
+        for (int t2 = 0; t2 < Q; t2++) dst[t2] = cmul(post[ga * Q2 + t1 * Q + t2], acc[t2]);
+      }
     }
   }
 }
+// Initialization CTA: one thread per (RHS, t1) row, kRMax q threads.
+template <int Q> struct InitShape {
+  static constexpr int threads = kRMax * Q;
+};
+constexpr int kInitChunk = 16;  // boxes A whose phases are staged together
 template <int Q>
-__global__ void __launch_bounds__(256) k32_init(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc, int GA,
-                                                 const float2 *__restrict__ f, float2 *__restrict__ st) {
+__global__ void __launch_bounds__(InitShape<Q>::threads) k32_init(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc,
+                                                                   int GA, const float2 *__restrict__ f,
+                                                                   float2 *__restrict__ st) {
   k32_init_body<Q>(tb, tf, ph, g, maxsrc, GA, f, st, blockIdx.x, blockIdx.y);
 }
 
@@ -826,19 +943,16 @@ __device__ __forceinline__ void k32_term_body(const Tables &tb, const TablesF &t
     const float2 *dv = dbuf + (B & 1) * kRMax * Q2;
     for (int task = threadIdx.x; task < rt * Q; task += blockDim.x) {
       const int t2 = task % Q, r = task / Q;
-      float yx[kTermM], yy[kTermM];
+      float2 ym[kTermM];
 #pragma unroll
-      for (int m = 0; m < kTermM; m++) yx[m] = yy[m] = 0.f;
+      for (int m = 0; m < kTermM; m++) ym[m] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int t1 = 0; t1 < Q; t1++) {
         const float2 c = cmul(pre[t1 * Q + t2], dv[r * Q2 + t1 * Q + t2]);
 #pragma unroll
-        for (int m = 0; m < kTermM; m++) {
-          yx[m] = __fmaf_rn(vm.V[m][t1], c.x, yx[m]);
-          yy[m] = __fmaf_rn(vm.V[m][t1], c.y, yy[m]);
-        }
+        for (int m = 0; m < kTermM; m++) ym[m] = fma2s(vm.V[m][t1], c, ym[m]);
       }
-      for (int m = 0; m < M; m++) y[(r * kTermM + m) * Q + t2] = make_float2(yx[m], yy[m]);
+      for (int m = 0; m < M; m++) y[(r * kTermM + m) * Q + t2] = ym[m];
     }
     __syncthreads();
     issue(B + 2);
@@ -849,12 +963,10 @@ __device__ __forceinline__ void k32_term_body(const Tables &tb, const TablesF &t
 #pragma unroll
       for (int m2 = 0; m2 < kTermM; m2++) {
         if (m2 < M) {
-          float wx = 0.f, wy = 0.f;
+          float2 wv = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int t2 = 0; t2 < Q; t2++) {
-            wx = __fmaf_rn(vm.V[m2][t2], yr[t2].x, wx);
-            wy = __fmaf_rn(vm.V[m2][t2], yr[t2].y, wy);
-          }
+          for (int t2 = 0; t2 < Q; t2++) wv = fma2s(vm.V[m2][t2], yr[t2], wv);
+          const float wx = wv.x, wy = wv.y;
           const float2 p = post[m1o * M + m2];
           ux[m2] = __fmaf_rn(p.x, wx, __fmaf_rn(-p.y, wy, ux[m2]));
           uy[m2] = __fmaf_rn(p.x, wy, __fmaf_rn(p.y, wx, uy[m2]));
@@ -938,19 +1050,16 @@ __device__ __forceinline__ void k32_term_adj_body(const Tables &tb, const Tables
     // y[r][t1][m2] = sum_m1 V[m1][t1] pre[m] g[r][m]   (thread per (r, m2))
     for (int task = threadIdx.x; task < rt * M; task += blockDim.x) {
       const int m2 = task % M, r = task / M;
-      float yx[Q], yy[Q];
+      float2 yv[Q];
 #pragma unroll
-      for (int t1 = 0; t1 < Q; t1++) yx[t1] = yy[t1] = 0.f;
+      for (int t1 = 0; t1 < Q; t1++) yv[t1] = make_float2(0.f, 0.f);
       for (int m1 = 0; m1 < M; m1++) {
         const float2 c = cmul(pre[m1 * M + m2], gv[r * M2 + m1 * M + m2]);
 #pragma unroll
-        for (int t1 = 0; t1 < Q; t1++) {
-          yx[t1] = __fmaf_rn(vm.V[m1][t1], c.x, yx[t1]);
-          yy[t1] = __fmaf_rn(vm.V[m1][t1], c.y, yy[t1]);
-        }
+        for (int t1 = 0; t1 < Q; t1++) yv[t1] = fma2s(vm.V[m1][t1], c, yv[t1]);
       }
 #pragma unroll
-      for (int t1 = 0; t1 < Q; t1++) y[(r * Q + t1) * kTermM + m2] = make_float2(yx[t1], yy[t1]);
+      for (int t1 = 0; t1 < Q; t1++) y[(r * Q + t1) * kTermM + m2] = yv[t1];
     }
     __syncthreads();
     // d[r][t1][t2] = post[t] sum_m2 V[m2][t2] y[r][t1][m2]   (thread per (r, t1))
@@ -962,13 +1071,10 @@ __device__ __forceinline__ void k32_term_adj_body(const Tables &tb, const Tables
       for (int m2 = 0; m2 < kTermM; m2++) yr[m2] = m2 < M ? y[(r * Q + t1) * kTermM + m2] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int t2 = 0; t2 < Q; t2++) {
-        float ax = 0.f, ay = 0.f;
+        float2 av = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int m2 = 0; m2 < kTermM; m2++) {
-          ax = __fmaf_rn(vm.V[m2][t2], yr[m2].x, ax);
-          ay = __fmaf_rn(vm.V[m2][t2], yr[m2].y, ay);
-        }
-        dst[r * Q2 + t1 * Q + t2] = cmul(post[t1 * Q + t2], make_float2(ax, ay));
+        for (int m2 = 0; m2 < kTermM; m2++) av = fma2s(vm.V[m2][t2], yr[m2], av);
+        dst[r * Q2 + t1 * Q + t2] = cmul(post[t1 * Q + t2], av);
       }
     }
   }

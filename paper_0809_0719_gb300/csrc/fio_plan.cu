@@ -550,13 +550,11 @@ int fio_check(fio_plan_t p, void *stream) {
 
 int fio_plan_set_switch(fio_plan_t p, int impl) {
   if (!p) return fail(FIO_EINVAL, "plan is NULL");
-  if (impl != 0 && impl != 1) return fail(FIO_EINVAL, "switch impl %d must be 0 or 1", impl);
+  if (impl < 0 || impl > 2) return fail(FIO_EINVAL, "switch impl %d must be 0, 1 or 2", impl);
   if (p->d.precision != FIO_F32) return fail(FIO_EINVAL, "only FIO_F32 plans have a choice of switch kernel");
-  if (impl == 1) {
-    int ok = 0;
-    dispatch(p->d, fio::RUN_TC_OK, nullptr, nullptr, 1, nullptr, -1, &ok);
-    if (!ok) return fail(FIO_EINVAL, "the tensor-core switch does not fit q=%d", p->d.q);
-  }
+  int avail = 0;
+  dispatch(p->d, fio::RUN_TC_OK, nullptr, nullptr, 1, nullptr, -1, &avail);
+  if (!(avail >> impl & 1)) return fail(FIO_EINVAL, "switch kernel %d does not fit q=%d", impl, p->d.q);
   p->d.switch_impl = impl;
   return FIO_OK;
 }

@@ -154,6 +154,18 @@ template <typename R, int Q> struct Runner {
 
   template <bool FWD> int sw(const CT *in, CT *out) {
     if constexpr (sizeof(R) == 4) {
+      if (fast32() && p.switch_impl == 2 && SwWs<Q>::smem <= p.smem_optin) {
+        const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
+        const long long nwork = pairs * ((nrhs + kRMax - 1) / kRMax);
+        const Geom g = geom(p.lm, kRMax, 1, pairs);
+        const unsigned grid = (unsigned)std::min<long long>(nwork, std::max(1, p.num_sms));
+        if (count_only) return check();
+        pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
+        auto k = k32_switch_ws<Q, FWD>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, SwWs<Q>::threads, SwWs<Q>::smem, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, nwork);
+        return check();
+      }
       const size_t smem_tc = TcShape<Q>::smem_bytes();
       if (fast32() && p.switch_impl == 1 && p.status && smem_tc <= (size_t)p.smem_optin) {
         const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
@@ -200,8 +212,7 @@ template <typename R, int Q> struct Runner {
     const int ms = std::max(1, p.maxsrc);
     if constexpr (sizeof(R) == 4) {
       if (fast32()) {
-        const int rt = std::min(nrhs, kRMax);
-        int GA = std::max(1, kThreads / (rt * Q));
+        int GA = std::min(kInitChunk, 1 << (2 * p.l0));
         auto bytes = [&](int ga) { return (ms * kRMax + ga * ms + ga * Q2) * 8 + ms * 2 * Q * 4; };
         while (bytes(GA) > p.smem_optin && GA > 1) GA--;
         if (bytes(GA) <= p.smem_optin) {
@@ -211,7 +222,8 @@ template <typename R, int Q> struct Runner {
           pre(K_INIT);
           auto k = k32_init<Q>;
           set_smem(k, p.smem_optin);
-          k<<<grid, 256, bytes(GA), st>>>(p.tb, p.tf, p.ph, g, ms, GA, (const float2 *)f, (float2 *)out);
+          k<<<grid, InitShape<Q>::threads, bytes(GA), st>>>(p.tb, p.tf, p.ph, g, ms, GA, (const float2 *)f,
+                                                             (float2 *)out);
           return check();
         }
       }
@@ -334,6 +346,19 @@ template <typename R, int Q> struct Runner {
   // not matter) and keep the faster: the FFMA vs the tensor-core switch, and 4- vs
   // 8-RHS translation subtiles (at the plan's first translation level).  Returns the
   // chosen switch implementation (0 or 1).
+  // Bit i set: switch implementation i can run this plan (0 FFMA, 1 tensor cores,
+  // 2 warp-specialised FFMA).
+  int switch_impls() const {
+    if constexpr (sizeof(R) != 4) {
+      return 1;
+    } else {
+      if (!fast32()) return 1;
+      int m = 1;
+      if (p.status && TcShape<Q>::smem_bytes() <= (size_t)p.smem_optin) m |= 2;
+      if (SwWs<Q>::smem <= p.smem_optin) m |= 4;
+      return m;
+    }
+  }
   template <typename F> float best_ms(F &&fn) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -369,14 +394,20 @@ template <typename R, int Q> struct Runner {
         }
         pm.trans_rs = t[0] < t[1] ? 4 : 8;
       }
-      if (!p.status || TcShape<Q>::smem_bytes() > (size_t)p.smem_optin) return 0;
-      float best[2];
-      for (int impl = 0; impl < 2; impl++) {
+      const int avail = switch_impls();
+      float best = 1e30f;
+      int pick = 0;
+      for (int impl = 0; impl < 3; impl++) {
+        if (!(avail >> impl & 1)) continue;
         pm.switch_impl = impl;
-        best[impl] = best_ms([&]() { sw<true>(s0, s1); });
+        const float ms = best_ms([&]() { sw<true>(s0, s1); });
+        if (ms < best) {
+          best = ms;
+          pick = impl;
+        }
       }
-      pm.switch_impl = best[1] < best[0] ? 1 : 0;
-      return pm.switch_impl;
+      pm.switch_impl = pick;
+      return pick;
     }
   }
 
@@ -433,9 +464,8 @@ int run_plan(const PlanDev &p, int kind, const void *in, void *out, int nrhs, cu
   const bool count = kind == RUN_COUNT_FWD || kind == RUN_COUNT_ADJ;
   Runner<R, Q> r(p, st, nrhs, count);
   int rc;
-  if (kind == RUN_TC_OK) {  // can this plan use the tensor-core switch?
-    if (launches)
-      *launches = sizeof(R) == 4 && p.tf.xnode && p.status && TcShape<Q>::smem_bytes() <= (size_t)p.smem_optin;
+  if (kind == RUN_TC_OK) {  // which switch implementations can this plan use (bit mask)?
+    if (launches) *launches = r.switch_impls();
     return 0;
   }
   if (kind == RUN_TUNE) {

@@ -170,7 +170,8 @@ class Plan:
         return out
 
     def set_switch(self, impl: int) -> None:
-        """fio_plan_set_switch: 0 = FP32 FMA switch kernel, 1 = tensor-core switch kernel."""
+        """fio_plan_set_switch: 0 = FP32 FMA switch kernel, 1 = tensor-core switch kernel,
+        2 = warp-specialised persistent FP32 FMA switch kernel."""
         _check(lib().fio_plan_set_switch(self._h, int(impl)))
         self.info.switch_impl = int(impl)
 

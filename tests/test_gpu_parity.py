@@ -46,6 +46,17 @@ def oracle_bf(oracle, N, q, phase, f, s, e):
     return _oracle_cache[key]
 
 
+def set_switch(fio, plan, sw, q):
+    """Force the FP32 switch kernel; the warp-specialised one needs two q^4 kernel
+    buffers in shared memory and does not fit q = 11."""
+    try:
+        plan.set_switch(sw)
+    except fio.FIOError:
+        if sw == 2 and q >= 11:
+            pytest.skip("the warp-specialised switch does not fit q=%d" % q)
+        raise
+
+
 def rel(a, b):
     a = np.asarray(a).ravel()
     b = np.asarray(b).ravel()
@@ -69,14 +80,15 @@ CASES = [
 
 @pytest.mark.parametrize("N,q,phase,s,e", CASES)
 @pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 5, None), ("f32", 3, 0), ("f32", 9, 0),
-                                          ("f32", 3, 1), ("f32", 33, 1)])
+                                          ("f32", 3, 1), ("f32", 33, 1), ("f32", 3, 2), ("f32", 33, 2)])
 def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, nrhs, sw):
-    # sw: switch kernel of the FP32 form (0 FP32 FMA, 1 tensor cores), forced past the autotuner
+    # sw: switch kernel of the FP32 form (0 FP32 FMA, 1 tensor cores, 2 warp-specialised FP32 FMA),
+    # forced past the autotuner
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
     try:
         if sw is not None:
-            plan.set_switch(sw)
+            set_switch(fio, plan, sw, q)
         F = gaussian_batch(N, range(100, 100 + nrhs))
         f = torch.from_numpy(F).to(plan.dtype).cuda()
         u = plan.apply(f).cpu().numpy()
@@ -91,13 +103,14 @@ def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, 
 
 
 @pytest.mark.parametrize("N,q,phase,s,e", [(64, 5, "ellipse", 0, 2), (128, 7, "circle", 3, 2), (32, 3, "separable", 0, 1)])
-@pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 3, None), ("f32", 10, 0), ("f32", 10, 1)])
+@pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 3, None), ("f32", 10, 0), ("f32", 10, 1),
+                                          ("f32", 10, 2)])
 def test_adjoint_matches_oracle_adjoint(fio, oracle, N, q, phase, s, e, prec, nrhs, sw):
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
     try:
         if sw is not None:
-            plan.set_switch(sw)
+            set_switch(fio, plan, sw, q)
         G = gaussian_batch(N, range(200, 200 + nrhs))
         g = torch.from_numpy(G).to(plan.dtype).cuda()
         fb = plan.adjoint(g).cpu().numpy()
@@ -124,13 +137,13 @@ def test_every_stage_matches_oracle(fio, oracle, N, q, s, e):
         plan.close()
 
 
-@pytest.mark.parametrize("prec,tol,sw", [("f64", 1e-12, None), ("f32", 1e-6, 0), ("f32", 1e-6, 1)])
+@pytest.mark.parametrize("prec,tol,sw", [("f64", 1e-12, None), ("f32", 1e-6, 0), ("f32", 1e-6, 1), ("f32", 1e-6, 2)])
 @pytest.mark.parametrize("N,q,e", [(64, 5, 2), (256, 9, 2)])
 def test_dot_test(fio, prec, tol, sw, N, q, e):
     plan = fio.Plan(N, q, "ellipse", ELL16, prec, nrhs_max=2, e=e)
     try:
         if sw is not None:
-            plan.set_switch(sw)
+            set_switch(fio, plan, sw, q)
         f = torch.from_numpy(gaussian_batch(N, [1, 2])).to(plan.dtype).cuda()
         g = torch.from_numpy(gaussian_batch(N, [3, 4])).to(plan.dtype).cuda()
         Bf = plan.apply(f).to(torch.complex128)
