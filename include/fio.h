@@ -134,7 +134,7 @@ typedef struct {
   int switch_impl;         /* FIO_F32: switch kernel chosen by fio_plan's autotuner,
                               0 = FP32 FMA (one pair per CTA), 1 = tensor cores (tcgen05,
                               split TF32), 2 = FP32 FMA, warp-specialised and persistent */
-  int trans_rs;            /* FIO_F32: right-hand sides per translation subtile (4 or 8),
+  int trans_rs;            /* FIO_F32: right-hand sides per translation subtile (2, 4 or 8),
                               chosen by fio_plan's autotuner */
 } fio_plan_info_t;
 

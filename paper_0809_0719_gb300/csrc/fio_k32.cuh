@@ -17,13 +17,17 @@ namespace fio {
 
 // Translation CTA shape for an RHS subtile of RS right-hand sides: 4 RS q threads
 // (rounded up to whole warps), shared memory: phases 20 q^2 | staging 2 x 4 RS q^2 |
-// intermediate 8 RS q^2 complex.
+// intermediate max(8 RS, 26) q^2 complex.
+// The intermediate area also serves as the phase scratch (26 q^2 complex at most).
+__host__ __device__ constexpr int trans32_zsize(int rs) { return 8 * rs > 26 ? 8 * rs : 26; }
+__host__ __device__ constexpr int trans32_smem_bytes(int q, int rs) {
+  return (20 + 8 * rs + trans32_zsize(rs)) * q * q * 8;
+}
 template <int Q, int RS> struct TransShape {
   static constexpr int threads = (4 * RS * Q + 31) / 32 * 32;
-  static constexpr int smem = (20 + 16 * RS) * Q * Q * 8;
-  static constexpr int min_blocks = RS >= 8 ? 2 : 4;
+  static constexpr int smem = trans32_smem_bytes(Q, RS);
+  static constexpr int min_blocks = RS >= 8 ? 2 : RS >= 4 ? 4 : 5;
 };
-__host__ __device__ constexpr int trans32_smem_bytes(int q, int rs) { return (20 + 16 * rs) * q * q * 8; }
 constexpr int kRMax = 32;   // RHS per CTA (grid.y covers the rest)
 
 // df tables of an FP32-form plan (same indexing as the FP64 tables in Tables).

@@ -126,7 +126,8 @@ template <typename R, int Q> struct Runner {
   template <bool TYPE_P, bool FWD> int trans(int l, const CT *in, CT *out) {
     if constexpr (sizeof(R) == 4) {
       if (fast32()) {
-        if (p.trans_rs == 4) return trans32<TYPE_P, FWD, 4>(l, (const CT *)in, out);
+        if (p.trans_rs == 2) return trans32<TYPE_P, FWD, 2>(l, in, out);
+        if (p.trans_rs == 4) return trans32<TYPE_P, FWD, 4>(l, in, out);
         return trans32<TYPE_P, FWD, 8>(l, in, out);
       }
     }
@@ -387,12 +388,17 @@ template <typename R, int Q> struct Runner {
       if (p.l1 > p.l0) {  // translation subtile width
         const int l = p.lm > p.l0 ? p.l0 + 1 : p.lm + 1;
         const bool tp = p.lm > p.l0;
-        float t[2];
-        for (int v = 0; v < 2; v++) {
-          pm.trans_rs = v ? 8 : 4;
-          t[v] = best_ms([&]() { tp ? trans<true, true>(l, s0, s1) : trans<false, true>(l, s0, s1); });
+        float best = 1e30f;
+        int pick = 8;
+        for (int rs : {2, 4, 8}) {
+          pm.trans_rs = rs;
+          const float ms = best_ms([&]() { tp ? trans<true, true>(l, s0, s1) : trans<false, true>(l, s0, s1); });
+          if (ms < best) {
+            best = ms;
+            pick = rs;
+          }
         }
-        pm.trans_rs = t[0] < t[1] ? 4 : 8;
+        pm.trans_rs = pick;
       }
       const int avail = switch_impls();
       float best = 1e30f;
