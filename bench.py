@@ -255,6 +255,10 @@ def run_ours(args, rank, world, dist):
     switch_impl = plan.info.switch_impl
     trans_rs = plan.info.trans_rs
     u32 = u[0].cpu().numpy()
+    # the adjoint apply (backward of the differentiable apply) on the same plan, outside the timed region
+    fbar = torch.empty_like(f)
+    ms_adj = tmax(time_steps(lambda: plan.adjoint(u, out=fbar), max(1, args.steps), max(3, args.warmup), torch))
+    del fbar
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     fh = torch.from_numpy(F).to(torch.complex64).pin_memory()
@@ -329,6 +333,8 @@ def run_ours(args, rank, world, dist):
         "fp64_form": {"value": out64, "unit": "outputs/s", "ms_per_step": ms64, "nrhs": 1, "dtype": "f64",
                       "rel_l2_err": err64},
         "speedup_f32_vs_f64_form": out32 / out64,
+        "adjoint": {"value": whole_job_rate(N * N * NRHS, ms_adj, world), "unit": "outputs/s", "ms_per_step": ms_adj,
+                    "what": "fio_apply_adjoint on the same plan (32 RHS)"},
         "accuracy_bar_met": err32 <= max(2 * err64, 1e-5),
         "e2e": {"value": whole_job_rate(N * N * NRHS, e2e_ms, world), "unit": "outputs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": N * N * NRHS * 8, "d2h_bytes_per_step": N * N * NRHS * 8,

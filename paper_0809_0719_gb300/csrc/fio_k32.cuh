@@ -956,7 +956,9 @@ __device__ __forceinline__ void k32_term_body(const Tables &tb, const TablesF &t
 #pragma unroll
         for (int m = 0; m < kTermM; m++) ym[m] = fma2s(vm.V[m][t1], c, ym[m]);
       }
-      for (int m = 0; m < M; m++) y[(r * kTermM + m) * Q + t2] = ym[m];
+#pragma unroll
+      for (int m = 0; m < kTermM; m++)
+        if (m < M) y[(r * kTermM + m) * Q + t2] = ym[m];
     }
     __syncthreads();
     issue(B + 2);
@@ -980,9 +982,12 @@ __device__ __forceinline__ void k32_term_body(const Tables &tb, const TablesF &t
   }
   if (owner) {
     const long long i1 = (long long)a1 * M + m1o;
-    for (int m2 = 0; m2 < M; m2++) {
-      const long long i2 = (long long)a2 * M + m2;
-      u[(long long)(r0 + rr) * NN + (i1 << g.L) + i2] = make_float2(ux[m2], uy[m2]);
+#pragma unroll
+    for (int m2 = 0; m2 < kTermM; m2++) {  // compile-time index: the accumulators stay in registers
+      if (m2 < M) {
+        const long long i2 = (long long)a2 * M + m2;
+        u[(long long)(r0 + rr) * NN + (i1 << g.L) + i2] = make_float2(ux[m2], uy[m2]);
+      }
     }
   }
 }
