@@ -254,6 +254,7 @@ def run_ours(args, rank, world, dist):
     launches_per_step = plan.kernel_launches(NRHS)
     switch_impl = plan.info.switch_impl
     trans_rs = plan.info.trans_rs
+    sw_tile = plan.info.switch_rhs_tile
     u32 = u[0].cpu().numpy()
     # the adjoint apply (backward of the differentiable apply) on the same plan, outside the timed region
     fbar = torch.empty_like(f)
@@ -342,6 +343,7 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": launches_per_step * args.steps,
         "switch_kernel": ["fp32_fma", "tcgen05_tf32", "fp32_fma_warp_specialised"][switch_impl] + " (plan autotuner)",
         "translation_rhs_subtile": trans_rs,
+        "switch_rhs_tile": sw_tile,
         "kernels": kernels,
         "roofline": roof,
         "peak_probes": probes,

@@ -136,6 +136,8 @@ typedef struct {
                               split TF32), 2 = FP32 FMA, warp-specialised and persistent */
   int trans_rs;            /* FIO_F32: right-hand sides per translation subtile (2, 4 or 8),
                               chosen by fio_plan's autotuner */
+  int switch_rhs_tile;     /* FIO_F32, switch kernels 0 and 2: right-hand sides per contraction
+                              task (4 or 8), chosen by fio_plan's autotuner */
 } fio_plan_info_t;
 
 /* fio_plan_info -- copy the plan's parameters and sizes into *info. */
@@ -152,6 +154,12 @@ int fio_check(fio_plan_t plan, void *stream);
  * FIO_EINVAL if the plan is FIO_F64 or the kernel does not fit this plan (its
  * shared memory need: 1 and 2 are not available for every q). */
 int fio_plan_set_switch(fio_plan_t plan, int impl);
+
+/* fio_plan_set_tuning -- override every choice of fio_plan's autotuner for an FIO_F32
+ * plan (a value of -1 keeps the current choice): switch_impl as fio_plan_set_switch,
+ * switch_rhs_tile 4 or 8 (kernel 0 only; kernel 2 uses 4), trans_rs 2, 4 or 8.
+ * FIO_EINVAL for FIO_F64 plans or values outside those sets. */
+int fio_plan_set_tuning(fio_plan_t plan, int switch_impl, int switch_rhs_tile, int trans_rs);
 
 /* fio_kernel_launches -- number of kernels one fio_apply (adjoint != 0: fio_apply_adjoint)
  * with nrhs right-hand sides enqueues. */

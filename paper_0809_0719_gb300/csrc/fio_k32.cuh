@@ -453,14 +453,14 @@ template <int Q> struct SwLayout {
   static constexpr int Q2 = Q * Q;
   static constexpr int OP = (Q2 + 3) / 4 * 4;
 };
-template <int Q, int KS>
+template <int Q, int KS, int RB>
 __device__ __forceinline__ void sw_contract(const float *kre, const float *kim, const float2 *in_s, int rc, int task,
-                                            float2 (&ax)[2][4], float2 (&ay)[2][4], int &og, int &rg, int &nrg,
+                                            float2 (&ax)[2][RB], float2 (&ay)[2][RB], int &og, int &rg, int &nrg,
                                             bool &live) {
   constexpr int Q2 = Q * Q, OP = SwLayout<Q>::OP;
   constexpr int NOG = SwShape<Q>::NOG;
   constexpr int CH = (Q2 + KS - 1) / KS;
-  nrg = (rc + 3) / 4;
+  nrg = (rc + RB - 1) / RB;
   live = task < NOG * nrg * KS;
   const int ks = task % KS, grp = task / KS;
   rg = grp % nrg;
@@ -468,10 +468,10 @@ __device__ __forceinline__ void sw_contract(const float *kre, const float *kim, 
 #pragma unroll
   for (int h = 0; h < 2; h++)
 #pragma unroll
-    for (int c_ = 0; c_ < 4; c_++) ax[h][c_] = ay[h][c_] = make_float2(0.f, 0.f);
-  int rr[4];
+    for (int c_ = 0; c_ < RB; c_++) ax[h][c_] = ay[h][c_] = make_float2(0.f, 0.f);
+  int rr[RB];
 #pragma unroll
-  for (int c_ = 0; c_ < 4; c_++) rr[c_] = min(rg + nrg * c_, rc - 1);
+  for (int c_ = 0; c_ < RB; c_++) rr[c_] = min(rg + nrg * c_, rc - 1);
   if (live) {
     const int i1 = min(Q2, (ks + 1) * CH);
     const float *kr = kre + og * 4, *ki = kim + og * 4;
@@ -481,11 +481,11 @@ __device__ __forceinline__ void sw_contract(const float *kre, const float *kim, 
       const float2 r23 = *reinterpret_cast<const float2 *>(kr + i * OP + 2);
       const float2 m01 = *reinterpret_cast<const float2 *>(ki + i * OP);
       const float2 m23 = *reinterpret_cast<const float2 *>(ki + i * OP + 2);
-      float2 iv[4];
+      float2 iv[RB];
 #pragma unroll
-      for (int c_ = 0; c_ < 4; c_++) iv[c_] = in_s[rr[c_] * Q2 + i];
+      for (int c_ = 0; c_ < RB; c_++) iv[c_] = in_s[rr[c_] * Q2 + i];
 #pragma unroll
-      for (int c_ = 0; c_ < 4; c_++) {
+      for (int c_ = 0; c_ < RB; c_++) {
         const float2 X = make_float2(iv[c_].x, iv[c_].x), Y = make_float2(iv[c_].y, iv[c_].y);
         const float2 NY = make_float2(-iv[c_].y, -iv[c_].y);
         ax[0][c_] = __ffma2_rn(r01, X, ax[0][c_]);
@@ -504,7 +504,7 @@ __device__ __forceinline__ void sw_contract(const float *kre, const float *kim, 
 #pragma unroll
     for (int h = 0; h < 2; h++)
 #pragma unroll
-      for (int c_ = 0; c_ < 4; c_++) {
+      for (int c_ = 0; c_ < RB; c_++) {
         ax[h][c_].x += __shfl_xor_sync(0xffffffffu, ax[h][c_].x, m);
         ax[h][c_].y += __shfl_xor_sync(0xffffffffu, ax[h][c_].y, m);
         ay[h][c_].x += __shfl_xor_sync(0xffffffffu, ay[h][c_].x, m);
@@ -578,25 +578,25 @@ template <int Q> __device__ __forceinline__ void sw_zero_pad(float *kre, float *
 }
 // Contraction by nthr threads (this one is task) into registers, then -- after
 // sync(), when no thread reads in_s any more -- the results into in_s as [r][o].
-template <int Q, typename Sync>
+template <int Q, int RB, typename Sync>
 __device__ __forceinline__ void sw_contract_store(const float *kre, const float *kim, float2 *in_s, int rc, int task,
-                                                  int nthr, Sync &&sync) {
+                                                     int nthr, Sync &&sync) {
   constexpr int Q2 = Q * Q;
   constexpr int NOG = SwShape<Q>::NOG;
-  const int nrg0 = (rc + 3) / 4;
-  float2 ax[2][4], ay[2][4];
+  const int nrg0 = (rc + RB - 1) / RB;
+  float2 ax[2][RB], ay[2][RB];
   int og, rg, nrg;
   bool live;
-  if (NOG * nrg0 * 8 <= nthr) sw_contract<Q, 8>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
-  else if (NOG * nrg0 * 4 <= nthr) sw_contract<Q, 4>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
-  else if (NOG * nrg0 * 2 <= nthr) sw_contract<Q, 2>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
-  else sw_contract<Q, 1>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
+  if (NOG * nrg0 * 8 <= nthr) sw_contract<Q, 8, RB>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
+  else if (NOG * nrg0 * 4 <= nthr) sw_contract<Q, 4, RB>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
+  else if (NOG * nrg0 * 2 <= nthr) sw_contract<Q, 2, RB>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
+  else sw_contract<Q, 1, RB>(kre, kim, in_s, rc, task, ax, ay, og, rg, nrg, live);
   sync();
   if (live) {
 #pragma unroll
     for (int h = 0; h < 2; h++)
 #pragma unroll
-      for (int c_ = 0; c_ < 4; c_++) {
+      for (int c_ = 0; c_ < RB; c_++) {
         const int o = og * 4 + 2 * h, r = rg + nrg * c_;
         if (r < rc) {
           if (o < Q2) in_s[r * Q2 + o] = make_float2(ax[h][c_].x, ay[h][c_].x);
@@ -606,13 +606,14 @@ __device__ __forceinline__ void sw_contract_store(const float *kre, const float 
   }
 }
 
+
 // ---------------------------------------------------------------------------
 // FP32 switch (eq. alg2m): one CTA per pair (A, B) at level lm and up to 32 RHS.
 //   FWD : out[t] = sum_s e(x^A_t, p^B_s) in[s];   !FWD: out[s] = sum_t conj e(x^A_t, p^B_s) in[t].
 // theta(x_t, p_s) = rho(s1) G(x_t, p2_{s2}): q^3 evaluations of G, q^4 products.
 // The input block arrives by cp.async while the kernel matrix is generated.
 // ---------------------------------------------------------------------------
-template <int Q, bool FWD>
+template <int Q, bool FWD, int RB = 4>
 __device__ __forceinline__ void k32_switch_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g,
                                                 const float2 *__restrict__ in, float2 *__restrict__ out, long long bx_, int by_) {
   constexpr int Q2 = Q * Q, OP = SwLayout<Q>::OP;
@@ -631,14 +632,14 @@ __device__ __forceinline__ void k32_switch_body(const Tables &tb, const TablesF 
   sw_fill<Q, FWD>(tb, tf, ph, g, sw_decode(g, pr), kre, kim, rho_s, threadIdx.x, blockDim.x, []() { __syncthreads(); });
   cp_async_wait(0);
   __syncthreads();
-  sw_contract_store<Q>(kre, kim, in_s, rc, threadIdx.x, blockDim.x, []() { __syncthreads(); });
+  sw_contract_store<Q, RB>(kre, kim, in_s, rc, threadIdx.x, blockDim.x, []() { __syncthreads(); });
   __syncthreads();
   store_run(out + pr * nrq + (long long)r0 * Q2, in_s, rc * Q2);
 }
-template <int Q, bool FWD>
-__global__ void __launch_bounds__(SwShape<Q>::threads, 2) k32_switch(Tables tb, TablesF tf, Phase ph, Geom g, const float2 *__restrict__ in,
-                                                   float2 *__restrict__ out) {
-  k32_switch_body<Q, FWD>(tb, tf, ph, g, in, out, blockIdx.x, blockIdx.y);
+template <int Q, bool FWD, int RB>
+__global__ void __launch_bounds__(SwShape<Q>::threads, RB == 4 ? 3 : 2)
+    k32_switch(Tables tb, TablesF tf, Phase ph, Geom g, const float2 *__restrict__ in, float2 *__restrict__ out) {
+  k32_switch_body<Q, FWD, RB>(tb, tf, ph, g, in, out, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -703,7 +704,7 @@ __global__ void __launch_bounds__(SwWs<Q>::threads, 1) k32_switch_ws(Tables tb, 
       const float *kre = kbuf + b * W::kfloats, *kim = kre + Q2 * OP;
       float2 *io = ibuf + b * W::ifloat2;
       named_sync(kBarFull0 + b, W::threads);
-      sw_contract_store<Q>(kre, kim, io, rc, task, W::cons, []() { named_sync(kBarCons, W::cons); });
+      sw_contract_store<Q, 4>(kre, kim, io, rc, task, W::cons, []() { named_sync(kBarCons, W::cons); });
       named_sync(kBarCons, W::cons);
       store_run(out + pr * nrq + (long long)r0 * Q2, io, rc * Q2, task, W::cons);
       if (s + 2 < nstage) named_arrive(kBarEmpty0 + b, W::threads);

@@ -363,6 +363,7 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   // autotune the FP32 switch on this plan's shapes (kept for every later apply)
   d.switch_impl = 0;
   d.trans_rs = 8;
+  d.sw_rb = 4;
   if (precision == FIO_F32) {
     int impl = 0;
     const int rc = dispatch(d, fio::RUN_TUNE, nullptr, nullptr, nrhs_max, nullptr, -1, &impl);
@@ -473,6 +474,7 @@ int fio_plan_info(fio_plan_t p, fio_plan_info_t *info) {
   info->max_box_sources = d.maxsrc;
   info->switch_impl = d.switch_impl;
   info->trans_rs = d.trans_rs;
+  info->switch_rhs_tile = d.sw_rb;
   return FIO_OK;
 }
 
@@ -556,6 +558,22 @@ int fio_plan_set_switch(fio_plan_t p, int impl) {
   dispatch(p->d, fio::RUN_TC_OK, nullptr, nullptr, 1, nullptr, -1, &avail);
   if (!(avail >> impl & 1)) return fail(FIO_EINVAL, "switch kernel %d does not fit q=%d", impl, p->d.q);
   p->d.switch_impl = impl;
+  return FIO_OK;
+}
+
+int fio_plan_set_tuning(fio_plan_t p, int switch_impl, int switch_rhs_tile, int trans_rs) {
+  if (!p) return fail(FIO_EINVAL, "plan is NULL");
+  if (p->d.precision != FIO_F32) return fail(FIO_EINVAL, "only FIO_F32 plans are tuned");
+  if (switch_rhs_tile != -1 && switch_rhs_tile != 4 && switch_rhs_tile != 8)
+    return fail(FIO_EINVAL, "switch_rhs_tile %d must be 4 or 8", switch_rhs_tile);
+  if (trans_rs != -1 && trans_rs != 2 && trans_rs != 4 && trans_rs != 8)
+    return fail(FIO_EINVAL, "trans_rs %d must be 2, 4 or 8", trans_rs);
+  if (switch_impl != -1) {
+    const int rc = fio_plan_set_switch(p, switch_impl);
+    if (rc) return rc;
+  }
+  if (switch_rhs_tile != -1) p->d.sw_rb = switch_rhs_tile;
+  if (trans_rs != -1) p->d.trans_rs = trans_rs;
   return FIO_OK;
 }
 

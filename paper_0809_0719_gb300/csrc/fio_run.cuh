@@ -38,7 +38,8 @@ struct PlanDev {
   int smem_optin;
   int num_sms;
   int switch_impl;  // FP32 switch: 0 FFMA kernel, 1 tensor-core kernel (chosen by the plan's autotuner)
-  int trans_rs;     // FP32 translations: RHS per subtile, 4 or 8 (chosen by the plan's autotuner)
+  int trans_rs;     // FP32 translations: RHS per subtile, 2, 4 or 8 (chosen by the plan's autotuner)
+  int sw_rb;        // FP32 FFMA switch: RHS per contraction task, 4 or 8 (chosen by the plan's autotuner)
   int *status;  // device status word: 1 = a bounded wait expired (read by fio_check)
   Prof *prof;   // NULL unless profiling was ever enabled
 };
@@ -186,7 +187,7 @@ template <typename R, int Q> struct Runner {
         dim3 grid((unsigned)pairs, (unsigned)((nrhs + kRMax - 1) / kRMax));
         if (count_only) return check();
         pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
-        auto k = k32_switch<Q, FWD>;
+        auto k = p.sw_rb == 8 ? k32_switch<Q, FWD, 8> : k32_switch<Q, FWD, 4>;
         set_smem(k, p.smem_optin);
         k<<<grid, SwShape<Q>::threads, smem32, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out);
         return check();
@@ -402,17 +403,23 @@ template <typename R, int Q> struct Runner {
       }
       const int avail = switch_impls();
       float best = 1e30f;
-      int pick = 0;
+      int pick = 0, pick_rb = 4;
       for (int impl = 0; impl < 3; impl++) {
         if (!(avail >> impl & 1)) continue;
-        pm.switch_impl = impl;
-        const float ms = best_ms([&]() { sw<true>(s0, s1); });
-        if (ms < best) {
-          best = ms;
-          pick = impl;
+        for (int rb : {4, 8}) {
+          if (impl != 0 && rb != 4) continue;  // only the one-pair-per-CTA kernel has both tiles
+          pm.switch_impl = impl;
+          pm.sw_rb = rb;
+          const float ms = best_ms([&]() { sw<true>(s0, s1); });
+          if (ms < best) {
+            best = ms;
+            pick = impl;
+            pick_rb = rb;
+          }
         }
       }
       pm.switch_impl = pick;
+      pm.sw_rb = pick_rb;
       return pick;
     }
   }

@@ -162,6 +162,26 @@ def test_dot_test(fio, prec, tol, sw, N, q, e):
         plan.close()
 
 
+@pytest.mark.parametrize("N,q,phase,nrhs", [(64, 9, "ellipse", 33), (128, 5, "circle", 7)])
+@pytest.mark.parametrize("sw,tile,rs", [(0, 4, 2), (0, 8, 4), (0, 8, 8), (2, 4, 8)])
+def test_every_tuning_choice_matches_oracle(fio, oracle, N, q, phase, nrhs, sw, tile, rs):
+    # the autotuner picks among these per plan; each must give the oracle's result
+    pid, prm = PH[phase]
+    plan = fio.Plan(N, q, pid, prm, "f32", nrhs_max=nrhs)
+    try:
+        plan.set_tuning(sw, tile, rs)
+        assert (plan.info.switch_impl, plan.info.switch_rhs_tile, plan.info.trans_rs) == (sw, tile, rs)
+        F = gaussian_batch(N, range(300, 300 + nrhs))
+        U = plan.apply(torch.from_numpy(F).to(plan.dtype).cuda()).cpu().numpy()
+        G = plan.adjoint(torch.from_numpy(F).to(plan.dtype).cuda()).cpu().numpy()
+        for r in (0, nrhs - 1):
+            assert rel(U[r], oracle_bf(oracle, N, q, phase, F[r], -1, 2)) < F32_TOL
+            ref = oracle.butterfly_adjoint(N, q, pid, list(prm), F[r])
+            assert rel(G[r], ref) < F32_TOL
+    finally:
+        plan.close()
+
+
 def test_zero_input_gives_zero_and_linearity(fio):
     N = 64
     plan = fio.Plan(N, 5, "ellipse", ELL16, "f64", nrhs_max=3)
