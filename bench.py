@@ -103,6 +103,11 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per launch at the N=1024, q=9, 32-RHS workload, from ncu captures of
+# the current kernels on smaller cases scaled by pairs x RHS (profiles/dram_traffic_small_cases.md).
+MEASURED_TRAFFIC = {"switch": 171.0e9, "trans_p": 172.3e9, "trans_x": 172.4e9, "init": 86.7e9, "term": 87.2e9}
+
+
 def kernel_flops_bytes(kind: str, info, nrhs: int) -> tuple[float, float]:
     """Algorithmic FP32 flops and HBM bytes of ONE launch of a kernel kind.
 
@@ -303,7 +308,7 @@ def run_ours(args, rank, world, dist):
         fl, by = kernel_flops_bytes(k, info, NRHS)
         avg = ms / n
         kernels[k] = {"launches": n, "ms_per_launch": avg, "share": None, "gflops": fl / (avg * 1e-3) / 1e9,
-                      "gbs": by / (avg * 1e-3) / 1e9}
+                      "gbs": by / (avg * 1e-3) / 1e9, "dram_bytes_measured": MEASURED_TRAFFIC.get(k)}
     tot = sum(v["ms_per_launch"] * v["launches"] for v in kernels.values())
     for v in kernels.values():
         v["share"] = v["ms_per_launch"] * v["launches"] / tot
@@ -312,7 +317,10 @@ def run_ours(args, rank, world, dist):
     dom_ms = kernels[dom]["ms_per_launch"]
     roof = {"kernel": dom, "bound": "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12,
             "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s", "frac": fl / (dom_ms * 1e-3) / FP32_PEAK,
-            "traffic": None, "peak_source": FP32_PEAK_NOTE + " (derived, not measured)",
+            "traffic": MEASURED_TRAFFIC.get(dom) if (N, Q, NRHS) == (1024, 9, 32) else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on a smaller "
+                              "case, scaled by pairs x RHS",
+            "peak_source": FP32_PEAK_NOTE + " (derived, not measured)",
             "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
             "hbm_achieved_gbs": by / (dom_ms * 1e-3) / 1e9}
     probes = {}
