@@ -161,6 +161,33 @@ int fio_plan_set_switch(fio_plan_t plan, int impl);
  * FIO_EINVAL for FIO_F64 plans or values outside those sets. */
 int fio_plan_set_tuning(fio_plan_t plan, int switch_impl, int switch_rhs_tile, int trans_rs);
 
+/*
+ * fio_direct -- the operator itself (eq. dfio), summed directly on the GPU at sampled
+ * grid points: out[r][i] = sum_k e^{2 pi i Phi(x_i,k)} f[r](k), x_i = the flat grid index
+ * xi[i] = i1 * N + i2.  Every term of the N^2 is evaluated (O(N^2) per point), the phase as
+ * the plan's butterfly does (double-float for FIO_F32, FP64 for FIO_F64) and the sum
+ * accumulated in FP64 in a fixed order.  The reference against which the error of
+ * eq. err is estimated.
+ *   f    DEVICE, (nrhs, N, N) in the plan's complex dtype; 1 <= nrhs <= 65535
+ *   xi   DEVICE, nx int64 flat indices in [0, N^2) (not checked on the device)
+ *   out  DEVICE, (nrhs, nx) complex128
+ * Enqueued on `stream`; does not synchronise.
+ */
+int fio_direct(fio_plan_t plan, const void *f, int nrhs, const long long *xi, int nx, void *out, void *stream);
+
+/*
+ * fio_plan_auto -- a plan whose q meets a target accuracy (Sec. 5: the error falls
+ * geometrically with q, so the paper's recipe is to raise q until eq. err is small
+ * enough).  For q = 3, 5, 7, 9, 11 in turn it builds the plan (arguments as fio_plan),
+ * applies it to a seeded complex white-noise input and estimates the relative L2 error of
+ * eq. err on nsample seeded grid points against fio_direct; it stops at the first q whose
+ * estimate is <= target.  *out receives that plan (or the q = 11 plan if none meets the
+ * target: then fio_last_error() says so), *q_out its q and *err_out the estimate.
+ * Synchronises the device; allocates and frees scratch for one input and one output.
+ */
+int fio_plan_auto(fio_plan_t *out, int N, int phase_id, const double *params, int nparams, int precision, int nrhs_max,
+                  int s, int e, double target, int nsample, unsigned long long seed, int *q_out, double *err_out);
+
 /* fio_kernel_launches -- number of kernels one fio_apply (adjoint != 0: fio_apply_adjoint)
  * with nrhs right-hand sides enqueues. */
 int fio_kernel_launches(fio_plan_t plan, int nrhs, int adjoint);

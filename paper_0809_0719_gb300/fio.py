@@ -75,6 +75,10 @@ def lib() -> ctypes.CDLL:
             L.fio_peak_probe.argtypes = [ip, ctypes.POINTER(ctypes.c_double)]
             L.fio_plan_set_switch.argtypes = [vp, ip]
             L.fio_plan_set_tuning.argtypes = [vp, ip, ip, ip]
+            L.fio_direct.argtypes = [vp, vp, ip, vp, ip, vp, vp]
+            L.fio_plan_auto.argtypes = [ctypes.POINTER(vp), ip, ip, ctypes.POINTER(ctypes.c_double), ip, ip, ip, ip,
+                                        ip, ctypes.c_double, ip, ctypes.c_ulonglong, ctypes.POINTER(ip),
+                                        ctypes.POINTER(ctypes.c_double)]
             L.fio_check.argtypes = [vp, vp]
             L.fio_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(ip), ip]
             L.fio_batch_destroy.argtypes = [vp]
@@ -168,6 +172,19 @@ class Plan:
         f = self._dev_tensor(f, "f")[:1].contiguous()
         out = torch.empty(self.info.pairs_per_level * self.q * self.q, dtype=torch.complex128, device=f.device)
         _check(lib().fio_debug_stage(self._h, f.data_ptr(), stage, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def direct(self, f: torch.Tensor, xi: torch.Tensor, stream=None) -> torch.Tensor:
+        """fio_direct: the direct sum of eq. dfio at flat grid indices xi (int64 CUDA tensor);
+        returns (nrhs, len(xi)) complex128."""
+        f = self._dev_tensor(f, "f")
+        if not isinstance(xi, torch.Tensor) or not xi.is_cuda or xi.dtype != torch.int64 or xi.dim() != 1:
+            raise TypeError("xi must be a 1-D int64 CUDA tensor")
+        xi = xi.contiguous()
+        nrhs = f.shape[0]
+        out = torch.empty(nrhs, xi.numel(), dtype=torch.complex128, device=f.device)
+        _check(lib().fio_direct(self._h, f.data_ptr(), nrhs, xi.data_ptr(), xi.numel(), out.data_ptr(),
+                                _stream_ptr(stream)))
         return out
 
     def set_switch(self, impl: int) -> None:
@@ -269,6 +286,29 @@ class Batch:
         """Per-plan (nrhs, N, N) views of a packed buffer."""
         return [packed[self.offsets[i]:self.offsets[i + 1]].view(self.nrhs[i], p.N, p.N)
                 for i, p in enumerate(self.plans)]
+
+
+def plan_auto(N: int, target: float, phase="ellipse", params=(2.0, 1.0, 16.0, 1.0), precision="f32",
+              nrhs_max: int = 1, s: int = -1, e: int = -1, nsample: int = 256, seed: int = 0):
+    """fio_plan_auto: the plan of the smallest q in (3, 5, 7, 9, 11) whose estimated error
+    (eq. err on nsample seeded points) meets target.  Returns (plan, q, estimated error)."""
+    L = lib()
+    pid = PHASES[phase] if isinstance(phase, str) else int(phase)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    prm = [] if pid == 0 else list(params)
+    arr = (ctypes.c_double * max(1, len(prm)))(*prm)
+    h = ctypes.c_void_p()
+    q = ctypes.c_int()
+    err = ctypes.c_double()
+    _check(L.fio_plan_auto(ctypes.byref(h), N, pid, arr, len(prm), prec, nrhs_max, s, e, float(target), nsample,
+                           seed, ctypes.byref(q), ctypes.byref(err)))
+    plan = Plan.__new__(Plan)
+    plan._h = h
+    plan.info = PlanInfo()
+    _check(L.fio_plan_info(h, ctypes.byref(plan.info)))
+    plan.N, plan.q = N, q.value
+    plan.dtype = torch.complex128 if prec == F64 else torch.complex64
+    return plan, q.value, err.value
 
 
 def peak_probe(kind: str) -> float:

@@ -84,3 +84,16 @@ def test_batch_calls_reject_bad_arguments_without_a_gpu(lib):
     assert lib.fio_batch_offsets(None, None) == -1
     assert lib.fio_batch_info(None, None) == -1
     assert lib.fio_batch_destroy(None) == 0
+
+
+def test_auto_and_direct_reject_bad_arguments_without_a_gpu(lib):
+    h = ctypes.c_void_p()
+    q = ctypes.c_int()
+    err = ctypes.c_double()
+    prm = (ctypes.c_double * 4)(2, 1, 16, 1)
+    assert lib.fio_plan_auto(None, 64, 1, prm, 4, 1, 1, -1, -1, 1e-3, 16, 0, ctypes.byref(q), ctypes.byref(err)) == -1
+    assert lib.fio_plan_auto(ctypes.byref(h), 48, 1, prm, 4, 1, 1, -1, -1, 1e-3, 16, 0, None, None) == -1  # N
+    assert lib.fio_plan_auto(ctypes.byref(h), 64, 1, prm, 4, 1, 1, -1, -1, 0.0, 16, 0, None, None) == -1   # target
+    assert lib.fio_plan_auto(ctypes.byref(h), 64, 1, prm, 4, 1, 1, -1, -1, 1e-3, 0, 0, None, None) == -1   # nsample
+    assert lib.fio_direct(None, None, 1, None, 1, None, None) == -1
+    assert lib.fio_plan_set_tuning(None, -1, -1, -1) == -1
