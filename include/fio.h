@@ -162,6 +162,24 @@ int fio_plan_set_switch(fio_plan_t plan, int impl);
 int fio_plan_set_tuning(fio_plan_t plan, int switch_impl, int switch_rhs_tile, int trans_rs);
 
 /*
+ * fio_apply_amplitude -- an FIO with a variable amplitude (eq. allfio),
+ *     u(x) = sum_k a(x,k) e^{2 pi i Phi(x,k)} f(k),  a(x,k) = sum_{t < nt} g_t(x) h_t(k),
+ * the separated form the paper gives for it: the nt products f_t = h_t f are the
+ * right-hand sides of ONE butterfly apply, so every phase evaluation is shared by all of
+ * them (the "vectorised" butterfly), then u = sum_t g_t (B f_t), summed over t in order.
+ * adjoint != 0 applies the conjugate transpose: fbar(k) = sum_x conj a(x,k)
+ * e^{-2 pi i Phi(x,k)} gin(x) = sum_t conj h_t(k) (B^H (conj g_t gin))(k).
+ *   in, out  DEVICE (nrhs, N, N) in the plan's complex dtype (f and u; gin and fbar)
+ *   g        DEVICE (nt, N, N): g_t on X, element (t, i1, i2)
+ *   h        DEVICE (nt, N, N): h_t on Omega, element (t, k1 + N/2, k2 + N/2)
+ *   nt, nrhs nt * nrhs <= nrhs_max
+ * Uses the plan's two staging buffers (allocated on first use, nrhs_max N^2 elements
+ * each): one call at a time per plan.
+ */
+int fio_apply_amplitude(fio_plan_t plan, const void *in, const void *g, const void *h, int nt, void *out, int nrhs,
+                        int adjoint, void *stream);
+
+/*
  * fio_direct -- the operator itself (eq. dfio), summed directly on the GPU at sampled
  * grid points: out[r][i] = sum_k e^{2 pi i Phi(x_i,k)} f[r](k), x_i = the flat grid index
  * xi[i] = i1 * N + i2.  Every term of the N^2 is evaluated (O(N^2) per point), the phase as

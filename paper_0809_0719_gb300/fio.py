@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
             L.fio_plan_set_switch.argtypes = [vp, ip]
             L.fio_plan_set_tuning.argtypes = [vp, ip, ip, ip]
             L.fio_direct.argtypes = [vp, vp, ip, vp, ip, vp, vp]
+            L.fio_apply_amplitude.argtypes = [vp, vp, vp, vp, ip, vp, ip, ip, vp]
             L.fio_plan_auto.argtypes = [ctypes.POINTER(vp), ip, ip, ctypes.POINTER(ctypes.c_double), ip, ip, ip, ip,
                                         ip, ctypes.c_double, ip, ctypes.c_ulonglong, ctypes.POINTER(ip),
                                         ctypes.POINTER(ctypes.c_double)]
@@ -172,6 +173,20 @@ class Plan:
         f = self._dev_tensor(f, "f")[:1].contiguous()
         out = torch.empty(self.info.pairs_per_level * self.q * self.q, dtype=torch.complex128, device=f.device)
         _check(lib().fio_debug_stage(self._h, f.data_ptr(), stage, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def apply_amplitude(self, x: torch.Tensor, g: torch.Tensor, h: torch.Tensor, adjoint: bool = False,
+                        out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """fio_apply_amplitude: the FIO with amplitude a(x,k) = sum_t g[t](x) h[t](k) (eq. allfio),
+        or its conjugate transpose.  x, out: (nrhs, N, N); g, h: (nt, N, N)."""
+        x = self._dev_tensor(x, "input")
+        g = self._dev_tensor(g, "g")
+        h = self._dev_tensor(h, "h")
+        if g.shape[0] != h.shape[0]:
+            raise ValueError("g and h must have the same number of terms")
+        out = torch.empty_like(x) if out is None else self._dev_tensor(out, "out")
+        _check(lib().fio_apply_amplitude(self._h, x.data_ptr(), g.data_ptr(), h.data_ptr(), g.shape[0], out.data_ptr(),
+                                         x.shape[0], int(adjoint), _stream_ptr(stream)))
         return out
 
     def direct(self, f: torch.Tensor, xi: torch.Tensor, stream=None) -> torch.Tensor:

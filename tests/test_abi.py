@@ -97,3 +97,7 @@ def test_auto_and_direct_reject_bad_arguments_without_a_gpu(lib):
     assert lib.fio_plan_auto(ctypes.byref(h), 64, 1, prm, 4, 1, 1, -1, -1, 1e-3, 0, 0, None, None) == -1   # nsample
     assert lib.fio_direct(None, None, 1, None, 1, None, None) == -1
     assert lib.fio_plan_set_tuning(None, -1, -1, -1) == -1
+
+
+def test_amplitude_rejects_bad_arguments_without_a_gpu(lib):
+    assert lib.fio_apply_amplitude(None, None, None, None, 1, None, 1, 0, None) == -1
