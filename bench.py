@@ -264,7 +264,16 @@ def run_ours(args, rank, world, dist):
     # the adjoint apply (backward of the differentiable apply) on the same plan, outside the timed region
     fbar = torch.empty_like(f)
     ms_adj = tmax(time_steps(lambda: plan.adjoint(u, out=fbar), max(1, args.steps), max(3, args.warmup), torch))
-    del fbar
+    # dot test at this size: <g, B f> against <B^H g, f> over all 32 RHS, g = the seeds 100..131
+    gdot = torch.from_numpy(gaussian_batch(N, range(100, 100 + NRHS))).to(torch.complex64).to(dev)
+    plan.apply(f, out=u)
+    plan.adjoint(gdot, out=fbar)
+    g64, bf = gdot.to(torch.complex128).flatten(), u.to(torch.complex128).flatten()
+    da = torch.vdot(g64, bf)
+    db = torch.vdot(fbar.to(torch.complex128).flatten(), f.to(torch.complex128).flatten())
+    dot = {"rel_to_inner_product": abs(da - db).item() / abs(da).item(),
+           "rel_to_norms": abs(da - db).item() / (g64.norm() * bf.norm()).item()}
+    del fbar, gdot, g64, bf
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     fh = torch.from_numpy(F).to(torch.complex64).pin_memory()
@@ -352,7 +361,7 @@ def run_ours(args, rank, world, dist):
                       "rel_l2_err": err64},
         "speedup_f32_vs_f64_form": out32 / out64,
         "adjoint": {"value": whole_job_rate(N * N * NRHS, ms_adj, world), "unit": "outputs/s", "ms_per_step": ms_adj,
-                    "what": "fio_apply_adjoint on the same plan (32 RHS)"},
+                    "what": "fio_apply_adjoint on the same plan (32 RHS)", "dot_test": dot},
         "amplitude": {"value": whole_job_rate(N * N * na, ms_amp, world), "unit": "outputs/s", "ms_per_step": ms_amp,
                       "what": "fio_apply_amplitude: %d inputs x %d separated amplitude terms (eq. allfio) as one "
                               "32-RHS butterfly" % (na, nt)},
@@ -361,7 +370,7 @@ def run_ours(args, rank, world, dist):
                 "h2d_bytes_per_step": N * N * NRHS * 8, "d2h_bytes_per_step": N * N * NRHS * 8,
                 "api": "fio_apply_host (pinned host buffers)"},
         "gpu_launches": launches_per_step * args.steps,
-        "switch_kernel": ["fp32_fma", "tcgen05_tf32", "fp32_fma_warp_specialised"][switch_impl] + " (plan autotuner)",
+        "switch_kernel": ["fp32_fma", "tcgen05_tf32_smem_a", "fp32_fma_warp_specialised", "tcgen05_tf32_tmem_a"][switch_impl] + " (plan autotuner)",
         "translation_rhs_subtile": trans_rs,
         "switch_rhs_tile": sw_tile,
         "kernels": kernels,

@@ -80,8 +80,8 @@ enum { FIO_PHASE_LINEAR = 0, FIO_PHASE_ELLIPSE = 1, FIO_PHASE_CIRCLE = 2, FIO_PH
  *   e         angular refinement of the T_P boxes: a box at level j has width
  *             2^-j in p1 and 2^-(j+e) in p2 (-1 = 2; 0 is the square-box
  *             statement of Sec. 1.1; 0 <= e <= 4)
- * For FIO_F32 it also times the two switch kernels (FP32 FMA and tensor-core) and
- * two translation subtile widths once on its own buffers and keeps the faster
+ * For FIO_F32 it also times the switch kernels (FP32 FMA and tensor-core variants) and
+ * the translation subtile widths once on its own buffers and keeps the fastest
  * (fio_plan_info().switch_impl, .trans_rs).
  * Allocates device memory on the current CUDA device; the plan may only be
  * used with that device current.  Returns FIO_EINVAL for bad arguments,
@@ -133,7 +133,9 @@ typedef struct {
   int max_box_sources;     /* most sources in one initialization box B */
   int switch_impl;         /* FIO_F32: switch kernel chosen by fio_plan's autotuner,
                               0 = FP32 FMA (one pair per CTA), 1 = tensor cores (tcgen05,
-                              split TF32), 2 = FP32 FMA, warp-specialised and persistent */
+                              split TF32, kernel matrix in shared memory), 2 = FP32 FMA,
+                              warp-specialised and persistent, 3 = tensor cores with the
+                              kernel matrix in tensor memory (persistent, one CTA per SM) */
   int trans_rs;            /* FIO_F32: right-hand sides per translation subtile (2, 4 or 8),
                               chosen by fio_plan's autotuner */
   int switch_rhs_tile;     /* FIO_F32, switch kernels 0 and 2: right-hand sides per contraction
@@ -150,7 +152,8 @@ int fio_plan_info(fio_plan_t plan, fio_plan_info_t *info);
 int fio_check(fio_plan_t plan, void *stream);
 
 /* fio_plan_set_switch -- override the autotuner's choice of the FIO_F32 switch
- * kernel: impl 0 = FP32 FMA, 1 = tensor cores, 2 = warp-specialised FP32 FMA.
+ * kernel: impl 0 = FP32 FMA, 1 = tensor cores (kernel matrix in shared memory),
+ * 2 = warp-specialised FP32 FMA, 3 = tensor cores (kernel matrix in tensor memory).
  * FIO_EINVAL if the plan is FIO_F64 or the kernel does not fit this plan (its
  * shared memory need: 1 and 2 are not available for every q). */
 int fio_plan_set_switch(fio_plan_t plan, int impl);

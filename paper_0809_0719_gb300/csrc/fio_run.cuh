@@ -37,7 +37,8 @@ struct PlanDev {
   double V[kMMax][kQMax];
   int smem_optin;
   int num_sms;
-  int switch_impl;  // FP32 switch: 0 FFMA kernel, 1 tensor-core kernel (chosen by the plan's autotuner)
+  int switch_impl;  // FP32 switch: 0 FFMA, 1 tensor cores (A in smem), 2 warp-specialised FFMA,
+                    // 3 tensor cores (A in tensor memory); chosen by the plan's autotuner
   int trans_rs;     // FP32 translations: RHS per subtile, 2, 4 or 8 (chosen by the plan's autotuner)
   int sw_rb;        // FP32 FFMA switch: RHS per contraction task, 4 or 8 (chosen by the plan's autotuner)
   int *status;  // device status word: 1 = a bounded wait expired (read by fio_check)
@@ -166,6 +167,19 @@ template <typename R, int Q> struct Runner {
         auto k = k32_switch_ws<Q, FWD>;
         set_smem(k, p.smem_optin);
         k<<<grid, SwWs<Q>::threads, SwWs<Q>::smem, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, nwork);
+        return check();
+      }
+      const size_t smem_tm = TmShape<Q>::smem_bytes();
+      if (fast32() && p.switch_impl == 3 && p.status && smem_tm <= (size_t)p.smem_optin) {
+        const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
+        const Geom g = geom(p.lm, kRMax, 1, pairs);
+        const long long nsu = pairs >> (p.L - p.lm);  // (box A, angular box) super-units
+        dim3 grid((unsigned)std::min<long long>(nsu, std::max(1, p.num_sms)), (unsigned)((nrhs + kRMax - 1) / kRMax));
+        if (count_only) return check();
+        pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
+        auto k = k32_switch_tm<Q, FWD>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, kTmThreads, smem_tm, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, p.status);
         return check();
       }
       const size_t smem_tc = TcShape<Q>::smem_bytes();
@@ -348,8 +362,9 @@ template <typename R, int Q> struct Runner {
   // not matter) and keep the faster: the FFMA vs the tensor-core switch, and 4- vs
   // 8-RHS translation subtiles (at the plan's first translation level).  Returns the
   // chosen switch implementation (0 or 1).
-  // Bit i set: switch implementation i can run this plan (0 FFMA, 1 tensor cores,
-  // 2 warp-specialised FFMA).
+  // Bit i set: switch implementation i can run this plan (0 FFMA, 1 tensor cores with
+  // the kernel matrix in shared memory, 2 warp-specialised FFMA, 3 tensor cores with
+  // the kernel matrix in tensor memory).
   int switch_impls() const {
     if constexpr (sizeof(R) != 4) {
       return 1;
@@ -358,6 +373,7 @@ template <typename R, int Q> struct Runner {
       int m = 1;
       if (p.status && TcShape<Q>::smem_bytes() <= (size_t)p.smem_optin) m |= 2;
       if (SwWs<Q>::smem <= p.smem_optin) m |= 4;
+      if (p.status && TmShape<Q>::smem_bytes() <= (size_t)p.smem_optin && (1 << (p.L - p.lm)) <= kTmNb1Max) m |= 8;
       return m;
     }
   }
@@ -404,7 +420,7 @@ template <typename R, int Q> struct Runner {
       const int avail = switch_impls();
       float best = 1e30f;
       int pick = 0, pick_rb = 4;
-      for (int impl = 0; impl < 3; impl++) {
+      for (int impl = 0; impl < 4; impl++) {
         if (!(avail >> impl & 1)) continue;
         for (int rb : {4, 8}) {
           if (impl != 0 && rb != 4) continue;  // only the one-pair-per-CTA kernel has both tiles

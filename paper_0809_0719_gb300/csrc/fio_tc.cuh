@@ -39,7 +39,8 @@ constexpr int kTcProducers = 256;               // 8 producer warps
 constexpr int kTcThreads = kTcProducers + 32;   // + 1 MMA warp
 constexpr int kTcKC = 16;                       // K columns per chunk (2 MMA K-steps)
 constexpr int kTcPA = 2, kTcPB = 3;             // TF32 parts of A (kernel) and B (coefficients)
-constexpr long long kTcSpin = 1LL << 24;        // bounded mbarrier polling (>= ~2 s with the back-off)
+constexpr unsigned long long kTcWaitNs = 2000000000ULL;  // bound of one mbarrier wait (2 s)
+constexpr uint32_t kTcSuspendNs = 1000000;               // suspend-time hint of one try_wait (1 ms)
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -51,17 +52,20 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 // D f32, A and B tf32, both K-major, N = 64, M = 128.
 constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
+// Round a finite FP32 value to TF32 (10 stored mantissa bits), to nearest with ties away
+// from zero: add half a TF32 unit to the magnitude bits and clear the 13 low bits (a
+// carry into the exponent is the correct round-up).  Two integer operations.
 __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
-// x = p0 + p1 (+ p2) with each part in TF32; the residual is ~2^-22 |x| (~2^-33 |x|).
+// x = p0 + p1 (+ p2) with p0, p1 rounded to TF32; the residual is ~2^-22 |x|.  With three
+// parts p2 is the exact remainder in FP32: the tensor core reads its leading TF32 bits
+// (truncation), so what it drops is ~2^-32 |x|.
 template <int P> __device__ __forceinline__ void tf32_split(float x, float *p) {
   p[0] = tf32_rna(x);
   float r = x - p[0];
   p[1] = tf32_rna(r);
-  if (P > 2) p[2] = tf32_rna(r - p[1]);
+  if (P > 2) p[2] = r - p[1];
 }
 __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
   asm volatile(
@@ -73,17 +77,27 @@ __device__ __forceinline__ void tc_commit(uint64_t *mbar) {
   const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
 }
-// Bounded wait for the completion of the mbarrier phase with the given parity.
+// Bounded wait for the completion of the mbarrier phase with the given parity:
+// mbarrier.try_wait suspends the thread in hardware until the phase completes or
+// the suspend-time hint passes, so the loop neither spins on the issue slots nor
+// sleeps past the completion; the bound is wall time.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity) {
   const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
-  uint32_t done = 0;
-  for (long long it = 0; it < kTcSpin; it++) {
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done)
-                 : "r"(mb), "r"(parity)
-                 : "memory");
+  const unsigned long long t0 = globaltimer_ns();
+  for (uint32_t it = 1; it < (1u << 26); it++) {  // the wall-time bound normally ends it first
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mb), "r"(parity), "r"(kTcSuspendNs)
+        : "memory");
     if (done) return true;
-    if (it > 2) __nanosleep(128);  // yield the issue slots to the warps doing work
+    if (globaltimer_ns() - t0 > kTcWaitNs) return false;
   }
   return false;
 }
@@ -345,6 +359,410 @@ __global__ void __launch_bounds__(kTcThreads, 2) k32_switch_tc(Tables tb, Tables
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
+// ---------------------------------------------------------------------------
+// Second tensor-core switch: the kernel matrix lives in tensor memory.
+//
+// Same real GEMM as above (A = kernel, M = q^2 rows padded to 128; B = the
+// coefficients in the [Re, Im; -Im, Re] form, N = 64; split TF32, 5 products),
+// but A never touches shared memory: the producer thread that owns row t of A
+// (TMEM lane t) computes its kernel entries and writes both TF32 parts to tensor
+// memory with tcgen05.st, and the MMA reads A from there (the [a-tmem] operand
+// form), so only B (2 KB per MMA) is read from shared memory.
+//
+// K is cut into chunks of kTmCK MMA K-steps.  A chunk occupies one A slot in
+// tensor memory (2 parts x kTmKC columns) and one B slot in shared memory (3
+// parts); kTmNB slots of each form a ring, so the producers run up to kTmNB
+// chunks ahead of the MMA warp.  Tensor memory (512 columns, one CTA per SM):
+// two 64-column accumulators (the epilogue of a pair overlaps the MMAs of the
+// next) and the A ring.  Per pair the producers first tabulate G(x_t, p2) (q^3
+// values, homogeneity of Phi) and prefetch the next pair's coefficients; each
+// kernel entry is then one double-float product, the exact reduction mod 1 and
+// the SFU sine/cosine.  Producer warps own TMEM lane quarters (warp % 4); the
+// kTmPQ warps of a quarter split a chunk's columns, and warps whose quarter holds
+// no row of A (q^2 <= 96 leaves quarter 3 empty) build B.
+//
+// Hand-offs are mbarriers (all waits bounded, warp-uniform outcome):
+//   full[j]   producers -> MMA   (arrive count kTmProducers) chunk in slot j written
+//   fre[j]    MMA -> producers   (tcgen05.commit)            slot j read
+//   dfull[d]  MMA -> producers   (tcgen05.commit)            accumulator d complete
+//   dempty[d] producers -> MMA   (arrive count kTmProducers) accumulator d read out
+//   tab[b]    producers          (arrive count kTmProducers) tables + inputs of a pair ready
+// ---------------------------------------------------------------------------
+constexpr int kTmProducers = 512;               // 16 producer warps, 4 per TMEM lane quarter
+constexpr int kTmThreads = kTmProducers + 32;   // + 1 MMA warp
+constexpr int kTmCK = 7;                        // MMA K-steps per chunk (q = 9: 3 chunks per pair)
+constexpr int kTmKC = 8 * kTmCK;                // K columns per chunk (28 complex kernel columns)
+constexpr int kTmNB = 3;                        // ring slots (A in TMEM, B in shared memory)
+constexpr int kTmDcols = 128;                   // two accumulators of 64 columns
+constexpr int kTmAcols = 2 * kTmKC;             // TMEM columns of one A slot (two TF32 parts)
+constexpr int kTmSmemFloor = 120 * 1024;        // > half an SM's shared memory: one CTA (512 TMEM columns) per SM
+constexpr int kTmNb1Max = 64;                   // radial boxes at the switch level (2^ceil(L/2), N <= 4096)
+static_assert(kTmDcols + kTmNB * kTmAcols <= 512, "tensor memory budget");
+constexpr int kTmPQ = kTmProducers / 128;        // producer warps per lane quarter
+static_assert(kTmProducers % 128 == 0 && (kTmKC / 2) % kTmPQ == 0, "producer warps split a chunk's columns evenly");
+
+template <int Q> struct TmShape {
+  static constexpr int Q2 = Q * Q;
+  static constexpr int KP = ((2 * Q2 + 7) / 8) * 8;        // padded K
+  static constexpr int KS = KP / 8;                        // MMA K-steps per pair
+  static constexpr int NCH = (KS + kTmCK - 1) / kTmCK;     // chunks per pair (the last may be partial)
+  static constexpr int B_FLOATS = 64 * kTmKC;              // one TF32 part of one B slot
+  static constexpr size_t b_bytes = (size_t)kTmNB * kTcPB * B_FLOATS * 4;
+  static constexpr size_t in_bytes = (size_t)2 * kRMax * Q2 * 8;
+  static constexpr size_t gt_bytes = (size_t)2 * Q2 * Q * sizeof(df);
+  static constexpr size_t rho_bytes = (size_t)kTmNb1Max * Q * sizeof(df);
+  static constexpr int nbar = 2 * kTmNB + 7;
+  static constexpr size_t used = b_bytes + in_bytes + gt_bytes + rho_bytes + nbar * 8 + 16;
+  static constexpr size_t smem_bytes() { return used > (size_t)kTmSmemFloor ? used : (size_t)kTmSmemFloor; }
+};
+
+__device__ __forceinline__ void tm_mma(uint32_t dtm, uint32_t atm, uint64_t db, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
+      "r"(atm), "l"(db), "r"(kTcIdesc), "r"(acc));
+}
+__device__ __forceinline__ void tm_st8(uint32_t taddr, const float *v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+__device__ __forceinline__ void tm_st4(uint32_t taddr, const float *v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(__float_as_uint(v[0])),
+               "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+               : "memory");
+}
+__device__ __forceinline__ void tm_st2(uint32_t taddr, const float *v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(__float_as_uint(v[0])),
+               "r"(__float_as_uint(v[1]))
+               : "memory");
+}
+// Store NC (a multiple of 2) consecutive columns of this warp's lanes.
+template <int NC> __device__ __forceinline__ void tm_st(uint32_t taddr, const float *v) {
+  static_assert(NC % 2 == 0, "column count");
+#pragma unroll
+  for (int c = 0; c + 8 <= NC; c += 8) tm_st8(taddr + c, v + c);
+  constexpr int O8 = NC / 8 * 8;
+  if constexpr (NC - O8 >= 4) tm_st4(taddr + O8, v + O8);
+  constexpr int O4 = NC - O8 >= 4 ? O8 + 4 : O8;
+  if constexpr (NC - O4 == 2) tm_st2(taddr + O4, v + O4);
+}
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 8; c++) v[c] = __uint_as_float(r[c]);
+}
+__device__ __forceinline__ void tm_arrive(uint64_t *mbar) { mbar_arrive(mbar); }
+
+template <int Q, bool FWD>
+__global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, TablesF tf, Phase ph, Geom g,
+                                                                const float2 *__restrict__ in,
+                                                                float2 *__restrict__ out, int *status) {
+  typedef TmShape<Q> S;
+  constexpr int Q2 = S::Q2, KS = S::KS, NCH = S::NCH;
+  constexpr int CPW = kTmKC / 2 / kTmPQ;  // complex kernel columns per producer warp and chunk
+  constexpr int RPW = kRMax / kTmPQ;      // RHS per producer warp in the epilogue
+  constexpr int KCC = kTmKC / 4;  // core-matrix columns (4 K each) per chunk
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // no-swizzle operands need 16-byte alignment
+  float *bs = (float *)smem_raw;                                   // B [slot][part][8 row groups][KCC][8][4]
+  float2 *instage = (float2 *)(smem_raw + S::b_bytes);             // [2][kRMax][Q2] coefficients
+  df *gt = (df *)(smem_raw + S::b_bytes + S::in_bytes);            // [2][Q2][Q] G(x_t, p2_s2)
+  df *rho = gt + 2 * Q2 * Q;                                       // [kTmNb1Max][Q] rho of every radial box
+  uint64_t *full = (uint64_t *)(rho + kTmNb1Max * Q);
+  uint64_t *fre = full + kTmNB;
+  uint64_t *dfull = fre + kTmNB;
+  uint64_t *dempty = dfull + 2;
+  uint64_t *tab = dempty + 2;
+  uint64_t *fin = tab + 2;
+  uint32_t *tmem_s = (uint32_t *)(fin + 1);
+  volatile int *abort_s = (volatile int *)(tmem_s + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int l = g.l, lb = g.L - g.l, e = g.e;
+  const int nb1 = 1 << lb, nb2 = 1 << (lb + e);
+  // Pair order: the pairs of one super-unit (box A, angular box b2) differ only in the
+  // radial box b1 and share G(x_t, p2); CTA c takes super-units c, c + gridDim.x, ...
+  // and within each all nb1 radial boxes.
+  // nb1 and nb2 are powers of two: every index below is a shift or a mask
+  const int lb2 = lb + e;  // log2 nb2
+  const long long nsu = g.nunits >> lb;
+  const int r0 = blockIdx.y * kRMax;
+  const int rc = min(kRMax, g.nrhs - r0);
+  const long long nrq = (long long)g.nrhs * Q2;
+  const bool sep = ph.id == 3;
+  auto su_of = [&](long long k) { return (long long)blockIdx.x + (k >> lb) * gridDim.x; };
+  auto pair_of = [&](long long k) {  // global pair index of the CTA's k-th pair
+    const long long su = su_of(k);
+    return ((su >> lb2) << (lb + lb2)) + ((k & (nb1 - 1)) << lb2) + (su & (nb2 - 1));
+  };
+
+  if (tid == 0) {
+    for (int b = 0; b < S::nbar; b++) {
+      const int cnt = (b < kTmNB || (b >= 2 * kTmNB + 2 && b < 2 * kTmNB + 6)) ? kTmProducers : 1;
+      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&full[b]);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(cnt));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_s = 0;
+  }
+  if (warp == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(tmem_s);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(dst));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_s;
+  // bounded wait with a warp-uniform outcome; on expiry record the status and raise the abort flag
+  auto waitw = [&](uint64_t *mb, uint32_t parity) {
+    bool ok = !*abort_s && tc_wait(mb, parity);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && lane == 0) {
+      atomicExch(status, 1);
+      *abort_s = 1;
+    }
+    return ok;
+  };
+
+  if (warp == kTmProducers / 32) {
+    // ------------------------------------------------------------ MMA warp
+    const uint32_t aB = (uint32_t)__cvta_generic_to_shared(bs);
+    constexpr uint32_t sbo = KCC * 128;
+    uint32_t gc = 0;
+    bool live = true;
+    for (long long k = 0; su_of(k) < nsu && live; k++) {
+      const int d = (int)(k & 1);
+      if (k >= 2 && !waitw(&dempty[d], (uint32_t)((k >> 1) - 1) & 1)) break;  // read-out of pair k - 2
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t dtm = tmem + 64 * d;
+      for (int c = 0; c < NCH; c++, gc++) {
+        const int j = (int)(gc % kTmNB);
+        if (!waitw(&full[j], (gc / kTmNB) & 1)) { live = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (lane == 0) {
+          const int nks = min(kTmCK, KS - c * kTmCK);
+          const uint32_t a0 = tmem + kTmDcols + j * kTmAcols;
+          for (int ks = 0; ks < nks; ks++) {
+            uint64_t dB[kTcPB];
+#pragma unroll
+            for (int q_ = 0; q_ < kTcPB; q_++)
+              dB[q_] = tc_desc(aB + ((j * kTcPB + q_) * S::B_FLOATS) * 4 + ks * 256, 128, sbo);
+            const uint32_t ta0 = a0 + 8 * ks, ta1 = a0 + kTmKC + 8 * ks;
+            tm_mma(dtm, ta0, dB[0], (c > 0 || ks > 0) ? 1u : 0u);
+            tm_mma(dtm, ta0, dB[1], 1u);
+            tm_mma(dtm, ta1, dB[0], 1u);
+            tm_mma(dtm, ta0, dB[2], 1u);
+            tm_mma(dtm, ta1, dB[1], 1u);
+          }
+          tc_commit(&fre[j]);
+          if (c == NCH - 1) tc_commit(&dfull[d]);
+        }
+        __syncwarp();
+      }
+    }
+    // drain: wait (bounded) until every MMA this warp issued has completed
+    if (lane == 0) tc_commit(fin);
+    __syncwarp();
+    if (!tc_wait(fin, 0) && lane == 0) atomicExch(status, 1);
+  } else {
+    // ------------------------------------------------------------ producer warps
+    const int qd = warp & 3, wh = warp >> 2;      // lane quarter, index among the quarter's warps
+    const int o = 32 * qd + lane;                 // TMEM lane = row of A
+    const bool arows = 32 * qd < Q2;              // this warp's quarter holds rows of A
+    const bool ovalid = o < Q2;
+    const int oc = ovalid ? o : Q2 - 1;           // clamped row for branch-free table reads
+    // B tasks (one core-matrix column kc of a chunk, all 64 rows): spread over the warps
+    // whose lane quarter holds no row of A, else over warps 0..KCC-1
+    int bidx = -1, bstride = 1;
+    {
+      const int nA = min(4, (Q2 + 31) / 32);
+      if (nA == 4) {
+        bidx = warp;
+        bstride = kTmProducers / 32;
+      } else {
+        const int per = 4 - nA;
+        if ((warp & 3) >= nA) bidx = (warp >> 2) * per + (warp & 3) - nA;
+        bstride = kTmPQ * per;
+      }
+    }
+    auto prefetch = [&](long long k, int slot) {
+      if (su_of(k) < nsu) {
+        const float2 *src = in + pair_of(k) * nrq + (long long)r0 * Q2;
+        for (int i = tid; i < rc * Q2; i += kTmProducers) cp_async8(instage + slot * kRMax * Q2 + i, src + i);
+      }
+      cp_async_commit();
+    };
+    auto tables = [&](long long k, int b) {  // G of the super-unit of pair k into gt[b]
+      if (sep) return;
+      const long long su = su_of(k);
+      const long long a = su >> lb2;
+      const int a1 = (int)(a >> l), a2 = (int)(a & ((1LL << l) - 1)), b2 = (int)(su & (nb2 - 1));
+      df *gtb = gt + b * Q2 * Q;
+      for (int idx = tid; idx < Q2 * Q; idx += kTmProducers) {
+        const int t = idx / Q, s2 = idx - t * Q;
+        const XDesc xdt = xdesc(tf.ph, xnf(tb, tf, l, a1, t / Q, Q), xnf(tb, tf, l, a2, t % Q, Q));
+        gtb[idx] = g_eval(tf.ph, xdt, p2f(tb, tf, lb, b2, s2, Q));
+      }
+    };
+    // phase parities: use k of tab[b] / dfull[d] (buffers alternate) belongs to pair 2k + index
+    auto epilogue = [&](long long k) {
+      const int d = (int)(k & 1);
+      if (!waitw(&dfull[d], (uint32_t)(k >> 1) & 1)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (arows) {
+        static_assert(RPW == 8, "epilogue reads 8 columns per warp");
+        const uint32_t trow = tmem + 64 * d + RPW * wh + ((uint32_t)(32 * qd) << 16);
+        float re[RPW], im[RPW];
+        tc_ld8(trow, re);
+        tc_ld8(trow + 32, im);
+        if (o < Q2) {
+          float2 *dst = out + pair_of(k) * nrq + (long long)(r0 + RPW * wh) * Q2 + o;
+#pragma unroll
+          for (int r = 0; r < RPW; r++)
+            if (RPW * wh + r < rc) dst[(long long)r * Q2] = make_float2(re[r], im[r]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      tm_arrive(&dempty[d]);
+      return true;
+    };
+
+    if (blockIdx.x < nsu) {
+      if (!sep)
+        for (int idx = tid; idx < nb1 * Q; idx += kTmProducers) rho[idx] = rhof(tb, tf, lb, idx / Q, idx % Q, Q);
+      prefetch(0, 0);
+      tables(0, 0);
+      cp_async_wait(0);
+      tm_arrive(&tab[0]);
+    }
+    uint32_t gc = 0;
+    long long k = 0;
+    bool live = true;
+    for (; su_of(k) < nsu && live; k++) {
+      const int b = (int)(k & 1);
+      if (!waitw(&tab[b], (uint32_t)(k >> 1) & 1)) break;
+      prefetch(k + 1, b ^ 1);
+      const float2 *ins = instage + b * kRMax * Q2;
+      const df *gtb = gt + (int)((k >> lb) & 1) * Q2 * Q;
+      const int b1 = (int)(k & (nb1 - 1));
+      const df *rhob = rho + b1 * Q;
+      int a1 = 0, a2 = 0, b2 = 0;
+      if (sep) {
+        const long long su = su_of(k), a = su >> lb2;
+        a1 = (int)(a >> l);
+        a2 = (int)(a & ((1LL << l) - 1));
+        b2 = (int)(su & (nb2 - 1));
+      }
+      // FWD: row o = x-node t, columns s walk (s1, s2); adjoint: row o = p-node s (fixed
+      // rho and s2), columns t walk G down a column
+      const df rho_row = (!FWD && !sep) ? rhob[oc / Q] : df{0.f, 0.f};
+      const df *grow = FWD ? gtb + oc * Q : gtb + oc % Q;
+      for (int c = 0; c < NCH; c++, gc++) {
+        const int j = (int)(gc % kTmNB);
+        if (gc >= kTmNB && !waitw(&fre[j], (gc / kTmNB - 1) & 1)) { live = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // A: this lane's row, CPW complex columns, both TF32 parts, into tensor memory.  The
+        // fast path is branch-free (indices clamped, invalid entries selected to zero) so the
+        // CPW independent phase chains interleave.
+        if (arows) {
+          float p0[2 * CPW], p1[2 * CPW];
+          const int i0 = c * (kTmKC / 2) + wh * CPW;  // first column of this warp
+#pragma unroll
+          for (int kk = 0; kk < CPW; kk++) {
+            const int i = i0 + kk;
+            const bool ok = ovalid && i < Q2;
+            const int ic = i < Q2 ? i : Q2 - 1;
+            float2 v;
+            if (!sep) {
+              df G, R;
+              if (FWD) {
+                const int s1 = ic / Q;
+                G = grow[ic - s1 * Q];
+                R = rhob[s1];
+              } else {
+                G = grow[ic * Q];
+                R = rho_row;
+              }
+              // theta = R G in double-float; (p - rint p) is exact, so the reduction mod 1
+              // needs no renormalisation of (p, lo)
+              const float p = R.h * G.h;
+              const float lo = __fmaf_rn(R.h, G.l, __fmaf_rn(R.l, G.h, __fmaf_rn(R.h, G.h, -p)));
+              const float r = (p - rintf(p)) + lo;
+              __sincosf(6.283185307179586f * r, &v.y, &v.x);
+            } else {
+              const int t = FWD ? oc : ic, s_ = FWD ? ic : oc;
+              v = expi<float>(theta_xp(ph, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q),
+                                       pn1(tb, lb, b1, s_ / Q, Q), pn2(tb, lb, b2, s_ % Q, Q)));
+            }
+            v.x = ok ? v.x : 0.f;
+            v.y = ok ? (FWD ? v.y : -v.y) : 0.f;
+            float pr_[kTcPA], pi_[kTcPA];
+            tf32_split<kTcPA>(v.x, pr_);
+            tf32_split<kTcPA>(v.y, pi_);
+            p0[2 * kk] = pr_[0];
+            p0[2 * kk + 1] = pi_[0];
+            p1[2 * kk] = pr_[1];
+            p1[2 * kk + 1] = pi_[1];
+          }
+          __syncwarp();
+          const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + kTmDcols + j * kTmAcols + 2 * CPW * wh;
+          tm_st<2 * CPW>(ta, p0);
+          tm_st<2 * CPW>(ta + kTmKC, p1);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        // B: lane r builds rows r and 32 + r of core-matrix column kc from X[r][s0], X[r][s0+1]
+        // (s0 = the chunk's first complex column + 2 kc): [Re, -Im] and [Im, Re], three TF32 parts
+        if (bidx >= 0) {
+          float *cb = bs + j * kTcPB * S::B_FLOATS;
+          for (int kc = bidx; kc < KCC; kc += bstride) {
+            const int s0 = c * (kTmKC / 2) + 2 * kc;
+            const int rr = lane < rc ? lane : 0;
+            float2 x0 = ins[rr * Q2 + min(s0, Q2 - 1)], x1 = ins[rr * Q2 + min(s0 + 1, Q2 - 1)];
+            if (!(lane < rc && s0 < Q2)) x0 = make_float2(0.f, 0.f);  // rows beyond rc were not loaded
+            if (!(lane < rc && s0 + 1 < Q2)) x1 = make_float2(0.f, 0.f);
+            float ar[kTcPB], ai[kTcPB], br[kTcPB], bi[kTcPB];
+            tf32_split<kTcPB>(x0.x, ar);
+            tf32_split<kTcPB>(x0.y, ai);
+            tf32_split<kTcPB>(x1.x, br);
+            tf32_split<kTcPB>(x1.y, bi);
+            float *top = cb + ((lane >> 3) * KCC + kc) * 32 + (lane & 7) * 4;
+            float *bot = top + 4 * KCC * 32;
+#pragma unroll
+            for (int q_ = 0; q_ < kTcPB; q_++) {
+              *reinterpret_cast<float4 *>(top + q_ * S::B_FLOATS) = make_float4(ar[q_], -ai[q_], br[q_], -bi[q_]);
+              *reinterpret_cast<float4 *>(bot + q_ * S::B_FLOATS) = make_float4(ai[q_], ar[q_], bi[q_], br[q_]);
+            }
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        tm_arrive(&full[j]);
+      }
+      if (!live) break;
+      if (k > 0 && !epilogue(k - 1)) break;
+      if (su_of(k + 1) < nsu) {
+        if (((k + 1) & (nb1 - 1)) == 0) tables(k + 1, (int)(((k + 1) >> lb) & 1));
+        cp_async_wait(0);
+        tm_arrive(&tab[b ^ 1]);
+      }
+    }
+    if (live && !*abort_s && k > 0) epilogue(k - 1);
+    cp_async_wait(0);
+  }
+  // the MMA warp has drained its MMAs (fin) and the producers their loads
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
 }  // namespace fio

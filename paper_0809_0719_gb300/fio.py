@@ -203,8 +203,9 @@ class Plan:
         return out
 
     def set_switch(self, impl: int) -> None:
-        """fio_plan_set_switch: 0 = FP32 FMA switch kernel, 1 = tensor-core switch kernel,
-        2 = warp-specialised persistent FP32 FMA switch kernel."""
+        """fio_plan_set_switch: 0 = FP32 FMA switch kernel, 1 = tensor-core switch kernel
+        (kernel matrix in shared memory), 2 = warp-specialised persistent FP32 FMA switch
+        kernel, 3 = tensor-core switch kernel with the kernel matrix in tensor memory."""
         _check(lib().fio_plan_set_switch(self._h, int(impl)))
         self.info.switch_impl = int(impl)
 

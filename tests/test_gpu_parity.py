@@ -80,9 +80,11 @@ CASES = [
 
 @pytest.mark.parametrize("N,q,phase,s,e", CASES)
 @pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 5, None), ("f32", 3, 0), ("f32", 9, 0),
-                                          ("f32", 3, 1), ("f32", 33, 1), ("f32", 3, 2), ("f32", 33, 2)])
+                                          ("f32", 3, 1), ("f32", 33, 1), ("f32", 3, 2), ("f32", 33, 2),
+                                          ("f32", 3, 3), ("f32", 33, 3)])
 def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, nrhs, sw):
-    # sw: switch kernel of the FP32 form (0 FP32 FMA, 1 tensor cores, 2 warp-specialised FP32 FMA),
+    # sw: switch kernel of the FP32 form (0 FP32 FMA, 1 tensor cores with the kernel matrix in
+    # shared memory, 2 warp-specialised FP32 FMA, 3 tensor cores with it in tensor memory),
     # forced past the autotuner
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
@@ -93,6 +95,7 @@ def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, 
         f = torch.from_numpy(F).to(plan.dtype).cuda()
         u = plan.apply(f).cpu().numpy()
         torch.cuda.synchronize()
+        plan.check()  # no bounded device-side wait expired
         tol = F64_TOL if prec == "f64" else F32_TOL
         for r in range(nrhs):
             ref = oracle_bf(oracle, N, q, phase, F[r].astype(np.complex64).astype(np.complex128) if prec == "f32" else F[r],
@@ -104,7 +107,7 @@ def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, 
 
 @pytest.mark.parametrize("N,q,phase,s,e", [(64, 5, "ellipse", 0, 2), (128, 7, "circle", 3, 2), (32, 3, "separable", 0, 1)])
 @pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 3, None), ("f32", 10, 0), ("f32", 10, 1),
-                                          ("f32", 10, 2)])
+                                          ("f32", 10, 2), ("f32", 10, 3)])
 def test_adjoint_matches_oracle_adjoint(fio, oracle, N, q, phase, s, e, prec, nrhs, sw):
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
@@ -114,6 +117,7 @@ def test_adjoint_matches_oracle_adjoint(fio, oracle, N, q, phase, s, e, prec, nr
         G = gaussian_batch(N, range(200, 200 + nrhs))
         g = torch.from_numpy(G).to(plan.dtype).cuda()
         fb = plan.adjoint(g).cpu().numpy()
+        plan.check()
         tol = F64_TOL if prec == "f64" else F32_TOL
         for r in range(nrhs):
             gr = G[r].astype(np.complex64).astype(np.complex128) if prec == "f32" else G[r]
@@ -137,7 +141,8 @@ def test_every_stage_matches_oracle(fio, oracle, N, q, s, e):
         plan.close()
 
 
-@pytest.mark.parametrize("prec,tol,sw", [("f64", 1e-12, None), ("f32", 1e-6, 0), ("f32", 1e-6, 1), ("f32", 1e-6, 2)])
+@pytest.mark.parametrize("prec,tol,sw", [("f64", 1e-12, None), ("f32", 1e-6, 0), ("f32", 1e-6, 1), ("f32", 1e-6, 2),
+                                         ("f32", 1e-6, 3)])
 @pytest.mark.parametrize("N,q,e", [(64, 5, 2), (256, 9, 2)])
 def test_dot_test(fio, prec, tol, sw, N, q, e):
     plan = fio.Plan(N, q, "ellipse", ELL16, prec, nrhs_max=2, e=e)
@@ -163,7 +168,7 @@ def test_dot_test(fio, prec, tol, sw, N, q, e):
 
 
 @pytest.mark.parametrize("N,q,phase,nrhs", [(64, 9, "ellipse", 33), (128, 5, "circle", 7)])
-@pytest.mark.parametrize("sw,tile,rs", [(0, 4, 2), (0, 8, 4), (0, 8, 8), (2, 4, 8)])
+@pytest.mark.parametrize("sw,tile,rs", [(0, 4, 2), (0, 8, 4), (0, 8, 8), (2, 4, 8), (3, 4, 4)])
 def test_every_tuning_choice_matches_oracle(fio, oracle, N, q, phase, nrhs, sw, tile, rs):
     # the autotuner picks among these per plan; each must give the oracle's result
     pid, prm = PH[phase]
@@ -277,3 +282,24 @@ def test_accuracy_against_direct_sum_medium(fio, oracle):
             plan.close()
     assert errs["f64"] < 3e-5
     assert errs["f32"] <= max(2 * errs["f64"], 1e-5)
+
+
+@pytest.mark.parametrize("N,q,nrhs", [(256, 9, 32), (256, 9, 7), (128, 11, 32), (256, 5, 40)])
+def test_tensor_memory_switch_matches_fma_switch(fio, N, q, nrhs):
+    # the persistent tensor-core switch walks hundreds of pairs per CTA (its tensor-memory
+    # and shared-memory rings wrap many times); forward and adjoint must agree with the FFMA
+    # switch on the same plan within the FP32 tolerance, with no bounded wait expiring
+    plan = fio.Plan(N, q, "ellipse", ELL16, "f32", nrhs_max=nrhs)
+    try:
+        f = torch.from_numpy(gaussian_batch(N, range(400, 400 + nrhs))).to(plan.dtype).cuda()
+        out = {}
+        for sw in (0, 3):
+            plan.set_switch(sw)
+            out[sw] = (plan.apply(f).to(torch.complex128), plan.adjoint(f).to(torch.complex128))
+            plan.check()
+        for k in range(2):
+            a, b = out[3][k], out[0][k]
+            for r in range(nrhs):
+                assert rel(a[r].cpu().numpy(), b[r].cpu().numpy()) < 2e-6, (k, r)
+    finally:
+        plan.close()
