@@ -37,6 +37,20 @@ FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"
 FP32_PEAK = 152 * 128 * 2 * 2.070e9
 
 
+def _tf32_peak_tflops() -> float:
+    """TF32 dense peak: the measured bf16 burst figure of MEASURED_PEAKS.json times the nominal
+    TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s); the recipe's fallback 1.9 PFLOP/s bf16 if absent."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        bf16 = 1900.0
+    return bf16 * 1.1 / 2.25
+
+
+TF32_PEAK_FROM_BF16 = _tf32_peak_tflops()
+
+
 def workload_config(precision="f32", nrhs=NRHS):
     return {"workload": "2D butterfly FIO apply N=%d q=%d ellipse[2,1,16,1] %d RHS %s form s=%d e=%d"
                         % (N, Q, nrhs, precision.upper(), S, E),
@@ -341,6 +355,19 @@ def run_ours(args, rank, world, dist):
             "peak_source": FP32_PEAK_NOTE + " (derived, not measured)",
             "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
             "hbm_achieved_gbs": by / (dom_ms * 1e-3) / 1e9}
+    # the whole apply against the same FP32 roofline: all kernels' algorithmic flops per step
+    apply_fl = sum(kernel_flops_bytes(k, info, NRHS)[0] * v["launches"] for k, v in kernels.items()) / args.steps
+    roof["apply_achieved"] = apply_fl / (ms32 * 1e-3) / 1e12
+    roof["apply_frac"] = apply_fl / (ms32 * 1e-3) / FP32_PEAK
+    if switch_impl in (1, 3) and "switch" in kernels:
+        # tensor-core switch: the MMA work it issues (M = 128 rows, N = 64, K = 2q^2 rounded up to 8,
+        # 5 split-TF32 products per pair) against the TF32 peak (measured bf16 x the nominal 1.1 / 2.25)
+        kp = (2 * Q * Q + 7) // 8 * 8
+        tc_fl = 5 * 2 * 128 * 64 * kp * info.pairs_per_level * ((NRHS + 31) // 32)
+        tf32_peak = TF32_PEAK_FROM_BF16 * 1e12
+        sw = kernels["switch"]
+        sw["tensor_tflops"] = tc_fl / (sw["ms_per_launch"] * 1e-3) / 1e12
+        sw["tensor_frac_of_tf32_peak"] = tc_fl / (sw["ms_per_launch"] * 1e-3) / tf32_peak
     probes = {}
     for kind in ("fp32", "fp64", "sfu"):
         try:
@@ -442,11 +469,14 @@ def run_small(args):
 
     n, r = args.small_n, args.small_nrhs
     plan = fio.Plan(n, Q, "ellipse", PARAMS, "f32", nrhs_max=r, s=S, e=E)
+    if args.switch_impl >= 0:
+        plan.set_switch(args.switch_impl)
     f = torch.from_numpy(gaussian_batch(n, range(r))).to(torch.complex64).cuda()
     u = torch.empty_like(f)
     ms = time_steps(lambda: plan.apply(f, out=u), args.steps, args.warmup, torch)
     msa = time_steps(lambda: plan.adjoint(u, out=f), args.steps, args.warmup, torch)
-    print(json.dumps({"case": "small", "N": n, "q": Q, "nrhs": r, "ms_forward": ms, "ms_adjoint": msa,
+    print(json.dumps({"case": "small", "N": n, "q": Q, "nrhs": r, "switch_impl": plan.info.switch_impl,
+                      "ms_forward": ms, "ms_adjoint": msa,
                       "launches_per_apply": plan.kernel_launches(r)}), flush=True)
     plan.close()
 
@@ -462,6 +492,8 @@ def main():
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the uneven-batch measurement")
     ap.add_argument("--small-n", type=int, default=256, help="--case small: N")
     ap.add_argument("--small-nrhs", type=int, default=16, help="--case small: right-hand sides")
+    ap.add_argument("--switch-impl", type=int, default=-1,
+                    help="--case small: force the FP32 switch kernel (fio_plan_set_switch), -1 = autotuner")
     args = ap.parse_args()
     if args.case == "small":
         run_small(args)
