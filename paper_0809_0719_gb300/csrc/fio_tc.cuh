@@ -1,6 +1,8 @@
 // fio_tc.cuh -- the FP32 form's switch (eq. alg2m) on the 5th-generation tensor
-// cores: tcgen05.mma kind::tf32 with operands in shared memory and the FP32
-// accumulator in tensor memory, as an error-compensated 3xTF32 product.
+// cores: tcgen05.mma kind::tf32 with the FP32 accumulator in tensor memory, as an
+// error-compensated split-TF32 product.  Two kernels: k32_switch_tc (both operands
+// staged in shared memory) and k32_switch_tm (the kernel matrix written straight to
+// tensor memory by the threads that compute it; the faster one at q = 9).
 //
 // Per pair (A, B) the switch is the complex product OUT[t][r] = sum_s K[t][s] IN[s][r]
 // (q^2 x q^2 kernel, up to 32 RHS).  It is posed as ONE real GEMM D = A B with
@@ -376,10 +378,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k32_switch_tc(Tables tb, Tables
 // parts); kTmNB slots of each form a ring, so the producers run up to kTmNB
 // chunks ahead of the MMA warp.  Tensor memory (512 columns, one CTA per SM):
 // two 64-column accumulators (the epilogue of a pair overlaps the MMAs of the
-// next) and the A ring.  Per pair the producers first tabulate G(x_t, p2) (q^3
-// values, homogeneity of Phi) and prefetch the next pair's coefficients; each
-// kernel entry is then one double-float product, the exact reduction mod 1 and
-// the SFU sine/cosine.  Producer warps own TMEM lane quarters (warp % 4); the
+// next) and the A ring.  Pairs are walked (box A, angular box of B) first and
+// radial box of B last; the producers tabulate G(x_t, p2) (q^3 values, homogeneity
+// of Phi) once per 2^l pairs that share it, keep rho(p1) of every radial box, and
+// prefetch the next pair's coefficients; each kernel entry is then one
+// double-float product, the exact reduction mod 1 and the SFU sine/cosine.  Producer warps own TMEM lane quarters (warp % 4); the
 // kTmPQ warps of a quarter split a chunk's columns, and warps whose quarter holds
 // no row of A (q^2 <= 96 leaves quarter 3 empty) build B.
 //
