@@ -61,6 +61,9 @@ def test_calls_on_null_plan_fail_cleanly(lib):
     assert lib.fio_apply(None, None, None, 1, None) == -1
     assert lib.fio_apply_adjoint(None, None, None, 1, None) == -1
     assert lib.fio_destroy(None) == 0
+    for impl in (0, 1, 2, 3):  # every switch kernel id, including the tensor-memory one
+        assert lib.fio_plan_set_switch(None, impl) == -1
+    assert lib.fio_plan_set_tuning(None, 3, -1, -1) == -1
 
 
 def test_binding_has_no_cpu_path():
