@@ -147,6 +147,49 @@ def kernel_flops_bytes(kind: str, info, nrhs: int) -> tuple[float, float]:
     return 0.0, 0.0
 
 
+def kernel_report(prof: dict, info, steps: int, ms_step: float, switch_impl: int) -> tuple[dict, dict]:
+    """Per-kernel breakdown of one timed apply and the dominant kernel's roofline.
+
+    prof: {kernel kind: (launches, total ms)} over `steps` applies of the headline plan (`info`
+    its PlanInfo); ms_step: CUDA-event time of one apply.  The roofline also carries the whole
+    apply's algorithmic flops against the same FP32 peak and, for a tensor-core switch, the
+    split-TF32 MMA work the switch issues against the TF32 peak."""
+    kernels = {}
+    for k, (n, ms) in prof.items():
+        fl, by = kernel_flops_bytes(k, info, NRHS)
+        avg = ms / n
+        kernels[k] = {"launches": n, "ms_per_launch": avg, "share": None, "gflops": fl / (avg * 1e-3) / 1e9,
+                      "gbs": by / (avg * 1e-3) / 1e9, "dram_bytes_measured": MEASURED_TRAFFIC.get(k)}
+    tot = sum(v["ms_per_launch"] * v["launches"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = v["ms_per_launch"] * v["launches"] / tot
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    fl, by = kernel_flops_bytes(dom, info, NRHS)
+    dom_ms = kernels[dom]["ms_per_launch"]
+    roof = {"kernel": dom, "bound": "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12,
+            "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s", "frac": fl / (dom_ms * 1e-3) / FP32_PEAK,
+            "traffic": MEASURED_TRAFFIC.get(dom) if (info.N, info.q, NRHS) == (1024, 9, 32) else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on a smaller "
+                              "case, scaled by pairs x RHS",
+            "peak_source": FP32_PEAK_NOTE + " (derived, not measured)",
+            "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
+            "hbm_achieved_gbs": by / (dom_ms * 1e-3) / 1e9}
+    # the whole apply against the same FP32 roofline: all kernels' algorithmic flops per step
+    apply_fl = sum(kernel_flops_bytes(k, info, NRHS)[0] * v["launches"] for k, v in kernels.items()) / steps
+    roof["apply_achieved"] = apply_fl / (ms_step * 1e-3) / 1e12
+    roof["apply_frac"] = apply_fl / (ms_step * 1e-3) / FP32_PEAK
+    if switch_impl in (1, 3) and "switch" in kernels:
+        # tensor-core switch: the MMA work it issues (M = 128 rows, N = 64, K = 2q^2 rounded up to 8,
+        # 5 split-TF32 products per pair) against the TF32 peak (measured bf16 x the nominal 1.1 / 2.25)
+        kp = (2 * info.q * info.q + 7) // 8 * 8
+        tc_fl = 5 * 2 * 128 * 64 * kp * info.pairs_per_level * ((NRHS + 31) // 32)
+        tf32_peak = TF32_PEAK_FROM_BF16 * 1e12
+        sw = kernels["switch"]
+        sw["tensor_tflops"] = tc_fl / (sw["ms_per_launch"] * 1e-3) / 1e12
+        sw["tensor_frac_of_tf32_peak"] = tc_fl / (sw["ms_per_launch"] * 1e-3) / tf32_peak
+    return kernels, roof
+
+
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
     """The largest x over all ranks (x itself without a process group)."""
     if dist is None:
@@ -334,40 +377,7 @@ def run_ours(args, rank, world, dist):
     out32 = whole_job_rate(N * N * NRHS, ms32, world)
     out64 = whole_job_rate(N * N, ms64, world)
 
-    # per-kernel breakdown and the dominant kernel's roofline
-    kernels = {}
-    for k, (n, ms) in prof.items():
-        fl, by = kernel_flops_bytes(k, info, NRHS)
-        avg = ms / n
-        kernels[k] = {"launches": n, "ms_per_launch": avg, "share": None, "gflops": fl / (avg * 1e-3) / 1e9,
-                      "gbs": by / (avg * 1e-3) / 1e9, "dram_bytes_measured": MEASURED_TRAFFIC.get(k)}
-    tot = sum(v["ms_per_launch"] * v["launches"] for v in kernels.values())
-    for v in kernels.values():
-        v["share"] = v["ms_per_launch"] * v["launches"] / tot
-    dom = max(kernels, key=lambda k: kernels[k]["share"])
-    fl, by = kernel_flops_bytes(dom, info, NRHS)
-    dom_ms = kernels[dom]["ms_per_launch"]
-    roof = {"kernel": dom, "bound": "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12,
-            "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s", "frac": fl / (dom_ms * 1e-3) / FP32_PEAK,
-            "traffic": MEASURED_TRAFFIC.get(dom) if (N, Q, NRHS) == (1024, 9, 32) else None,
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on a smaller "
-                              "case, scaled by pairs x RHS",
-            "peak_source": FP32_PEAK_NOTE + " (derived, not measured)",
-            "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
-            "hbm_achieved_gbs": by / (dom_ms * 1e-3) / 1e9}
-    # the whole apply against the same FP32 roofline: all kernels' algorithmic flops per step
-    apply_fl = sum(kernel_flops_bytes(k, info, NRHS)[0] * v["launches"] for k, v in kernels.items()) / args.steps
-    roof["apply_achieved"] = apply_fl / (ms32 * 1e-3) / 1e12
-    roof["apply_frac"] = apply_fl / (ms32 * 1e-3) / FP32_PEAK
-    if switch_impl in (1, 3) and "switch" in kernels:
-        # tensor-core switch: the MMA work it issues (M = 128 rows, N = 64, K = 2q^2 rounded up to 8,
-        # 5 split-TF32 products per pair) against the TF32 peak (measured bf16 x the nominal 1.1 / 2.25)
-        kp = (2 * Q * Q + 7) // 8 * 8
-        tc_fl = 5 * 2 * 128 * 64 * kp * info.pairs_per_level * ((NRHS + 31) // 32)
-        tf32_peak = TF32_PEAK_FROM_BF16 * 1e12
-        sw = kernels["switch"]
-        sw["tensor_tflops"] = tc_fl / (sw["ms_per_launch"] * 1e-3) / 1e12
-        sw["tensor_frac_of_tf32_peak"] = tc_fl / (sw["ms_per_launch"] * 1e-3) / tf32_peak
+    kernels, roof = kernel_report(prof, info, args.steps, ms32, switch_impl)
     probes = {}
     for kind in ("fp32", "fp64", "sfu"):
         try:
