@@ -181,6 +181,31 @@ def butterfly_adjoint(N, q, phase_id, params, g, s=-1, lm=-1, e=2) -> np.ndarray
     return out
 
 
+def wave_params(a, m, b, t, sign) -> list:
+    """Circle-phase constants [a, m, b, lambda] of Phi_sign(x, k) = x.k + sign c(x)|k| t with
+    c(x) = (a + m sin 2 pi x1 sin 2 pi x2) / b (the speed of eq. ex2), sign = +1 or -1."""
+    return [sign * a * t, sign * m * t, b, 1.0]
+
+
+def wave_direct(N, a, m, b, t, f, xi=None) -> np.ndarray:
+    """The wave-equation solution operator as a sum of two FIOs (Sec. 1): for u_tt = c^2 Lap u,
+    u(x, 0) = u0, u_t(x, 0) = 0 and f the Fourier coefficients of u0 on the lattice,
+        u(x, t) = 1/2 sum_k (e^{2 pi i Phi_+(x,k)} + e^{2 pi i Phi_-(x,k)}) f(k),
+    Phi_+-(x, k) = x.k +- c|k| t; exact for constant c (m = 0).  With m != 0 the two phases
+    use the variable speed c(x), the form of eq. ex2 (the paper notes the exact phases for
+    variable c solve a Hamilton-Jacobi equation; this is the two-phase FIO pair, not them)."""
+    up = direct(N, CIRCLE, wave_params(a, m, b, t, +1), f, xi)
+    um = direct(N, CIRCLE, wave_params(a, m, b, t, -1), f, xi)
+    return 0.5 * (up + um)
+
+
+def wave_butterfly(N, q, a, m, b, t, f, s=-1, lm=-1, e=2) -> np.ndarray:
+    """The same two-phase sum with each FIO applied by the butterfly (Sec. 4)."""
+    up = butterfly(N, q, CIRCLE, wave_params(a, m, b, t, +1), f, s=s, lm=lm, e=e)
+    um = butterfly(N, q, CIRCLE, wave_params(a, m, b, t, -1), f, s=s, lm=lm, e=e)
+    return 0.5 * (up + um)
+
+
 def rel_l2(a, b) -> float:
     """Relative L2 error of eq. err: ||a - b|| / ||b||."""
     a = np.asarray(a).ravel()

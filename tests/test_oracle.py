@@ -51,6 +51,29 @@ def test_direct_circle_with_constant_speed_is_a_dft(oracle, N):
     assert oracle.rel_l2(u, dft_of(f * np.exp(2j * np.pi * c * kk))) < 1e-12
 
 
+@pytest.mark.parametrize("t", [0.0, 0.37, 2.5])
+def test_wave_with_constant_speed_is_a_cosine_multiplier(oracle, t):
+    # u_tt = c^2 Lap u with u_t(x, 0) = 0: every Fourier mode of u0 evolves as cos(2 pi c |k| t)
+    # (Sec. 1), so the two-phase sum 1/2 (e^{2 pi i (x.k + c|k|t)} + e^{2 pi i (x.k - c|k|t)})
+    # must be the DFT of f(k) cos(2 pi c |k| t)
+    N, a, b = 16, 3.0, 20.0
+    f = gaussian_sources(N, 14)
+    k = np.arange(N) - N // 2
+    kk = np.sqrt(k[:, None] ** 2 + k[None, :] ** 2)
+    u = oracle.wave_direct(N, a, 0.0, b, t, f).reshape(N, N)
+    assert oracle.rel_l2(u, dft_of(f * np.cos(2 * np.pi * (a / b) * t * kk))) < 1e-12
+
+
+def test_wave_butterfly_error_falls_with_q(oracle):
+    # variable speed c(x) = (3 + sin sin)/20 at t = 1 (the phase pair of eq. ex2): each FIO by the
+    # butterfly; the error against the two-phase direct sum falls geometrically with q (Sec. 5)
+    N = 64
+    f = gaussian_sources(N, 15)
+    ud = oracle.wave_direct(N, 3.0, 1.0, 20.0, 1.0, f).reshape(N, N)
+    err = [oracle.rel_l2(oracle.wave_butterfly(N, q, 3.0, 1.0, 20.0, 1.0, f), ud) for q in (5, 7, 9)]
+    assert err[0] < 1e-2 and err[1] < err[0] / 10 and err[2] < err[1] / 10 and err[2] < 1e-5, err
+
+
 @pytest.mark.parametrize("N", [8, 32])
 def test_direct_adjoint_linear_phase_is_a_forward_dft(oracle, N):
     g = gaussian_sources(N, 13)
