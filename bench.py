@@ -369,6 +369,9 @@ def run_ours(args, rank, world, dist):
     del f64, u64
     torch.cuda.empty_cache()
 
+    # ---- the wave propagator as a sum of two FIOs (every rank: replicas)
+    wave = run_wave(args, dev, tmax, world)
+
     # ---- the uneven batch of plans (every rank: replicas)
     ub = run_uneven_batch(args, dev, with_errors=rank == 0) if args.batch else None
 
@@ -416,8 +419,45 @@ def run_ours(args, rank, world, dist):
         "cpu_baseline": base,
         "clocks": clk.summary(),
         "uneven_batch": ub,
+        "wave": wave,
     }
     print(json.dumps(line), flush=True)
+
+
+WAVE_N = 512  # two 32-RHS plans of this size hold 87 GB of state
+
+
+def run_wave(args, dev, tmax, world):
+    """fio_apply_wave: u = 1/2 (B_+ f + B_- f) with the circle phases x.k +- c(x)|k|t,
+    c(x) = (3 + sin 2 pi x1 sin 2 pi x2)/20, t = 1 (Sec. 1), N = WAVE_N, q = 9, 32 RHS, FP32
+    form.  A failure is reported in the result instead of raised, so the headline line is
+    printed whatever happens here."""
+    import torch
+
+    from paper_0809_0719_gb300 import fio
+    from paper_0809_0719_gb300.inputs import gaussian_batch
+
+    n = WAVE_N
+    plans = []
+    try:
+        plans = list(fio.wave_plans(n, Q, 3.0, 1.0, 20.0, 1.0, "f32", nrhs_max=NRHS, s=S, e=E))
+        f = torch.from_numpy(gaussian_batch(n, range(NRHS))).to(torch.complex64).to(dev)
+        u = torch.empty_like(f)
+        ms = tmax(time_steps(lambda: fio.apply_wave(plans[0], plans[1], f, out=u), max(1, args.steps),
+                             max(3, args.warmup), torch))
+        for p in plans:
+            p.check()
+        del f, u
+        return {"workload": "wave propagator u = (B+ f + B- f)/2, phases x.k +- c(x)|k|t, c = (3 + sin sin)/20, "
+                            "t = 1, N=%d q=%d %d RHS, FP32 form" % (n, Q, NRHS),
+                "value": whole_job_rate(n * n * NRHS, ms, world), "unit": "outputs/s", "ms_per_step": ms,
+                "api": "fio_apply_wave (two plans, one weighted-sum kernel)"}
+    except Exception as ex:  # reported, not raised
+        return {"error": "%s: %s" % (type(ex).__name__, ex)}
+    finally:
+        for p in plans:
+            p.close()
+        torch.cuda.empty_cache()
 
 
 def run_uneven_batch(args, dev, with_errors=True):

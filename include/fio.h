@@ -183,6 +183,24 @@ int fio_apply_amplitude(fio_plan_t plan, const void *in, const void *g, const vo
                         int adjoint, void *stream);
 
 /*
+ * fio_apply_wave -- a sum of two FIOs on the same input (Sec. 1: the solution operator of
+ * the wave equation u_tt = c^2 Lap u with u_t(x, 0) = 0 is
+ *     u(x, t) = 1/2 sum_k (e^{2 pi i (x.k + c|k|t)} + e^{2 pi i (x.k - c|k|t)}) f(k),
+ * f the Fourier coefficients of u(x, 0); with FIO_PHASE_CIRCLE plans of params
+ * [+a t, +m t, b, 1] and [-a t, -m t, b, 1] this is that pair, with the speed
+ * c(x) = (a + m sin 2 pi x1 sin 2 pi x2)/b):
+ *     out = w_plus B_plus in + w_minus B_minus in          (adjoint == 0)
+ *     out = w_plus B_plus^H in + w_minus B_minus^H in      (adjoint != 0)
+ *   plus, minus  plans of the same N, precision and device (any phases)
+ *   in, out      DEVICE (nrhs, N, N) in the plans' complex dtype, different buffers
+ *   nrhs         1 <= nrhs <= both plans' nrhs_max
+ * B_minus's result goes through the minus plan's first staging buffer (allocated on first
+ * use): one call at a time per plan.  Enqueued on `stream`.
+ */
+int fio_apply_wave(fio_plan_t plus, fio_plan_t minus, const void *in, void *out, int nrhs, double w_plus,
+                   double w_minus, int adjoint, void *stream);
+
+/*
  * fio_direct -- the operator itself (eq. dfio), summed directly on the GPU at sampled
  * grid points: out[r][i] = sum_k e^{2 pi i Phi(x_i,k)} f[r](k), x_i = the flat grid index
  * xi[i] = i1 * N + i2.  Every term of the N^2 is evaluated (O(N^2) per point), the phase as

@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
             L.fio_plan_set_tuning.argtypes = [vp, ip, ip, ip]
             L.fio_direct.argtypes = [vp, vp, ip, vp, ip, vp, vp]
             L.fio_apply_amplitude.argtypes = [vp, vp, vp, vp, ip, vp, ip, ip, vp]
+            L.fio_apply_wave.argtypes = [vp, vp, vp, vp, ip, ctypes.c_double, ctypes.c_double, ip, vp]
             L.fio_plan_auto.argtypes = [ctypes.POINTER(vp), ip, ip, ctypes.POINTER(ctypes.c_double), ip, ip, ip, ip,
                                         ip, ctypes.c_double, ip, ctypes.c_ulonglong, ctypes.POINTER(ip),
                                         ctypes.POINTER(ctypes.c_double)]
@@ -325,6 +326,26 @@ def plan_auto(N: int, target: float, phase="ellipse", params=(2.0, 1.0, 16.0, 1.
     plan.N, plan.q = N, q.value
     plan.dtype = torch.complex128 if prec == F64 else torch.complex64
     return plan, q.value, err.value
+
+
+def wave_plans(N: int, q: int, a: float, m: float, b: float, t: float, precision="f32", nrhs_max: int = 1,
+               s: int = -1, e: int = -1):
+    """The two circle-phase plans of the wave propagator at time t (Sec. 1): phases
+    x.k + c(x)|k|t and x.k - c(x)|k|t, c(x) = (a + m sin 2 pi x1 sin 2 pi x2)/b."""
+    plus = Plan(N, q, "circle", (a * t, m * t, b, 1.0), precision, nrhs_max, s, e)
+    minus = Plan(N, q, "circle", (-a * t, -m * t, b, 1.0), precision, nrhs_max, s, e)
+    return plus, minus
+
+
+def apply_wave(plus: Plan, minus: Plan, x: torch.Tensor, w_plus: float = 0.5, w_minus: float = 0.5,
+               adjoint: bool = False, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """fio_apply_wave: out = w_plus B_plus x + w_minus B_minus x (or the sum of the adjoints);
+    with wave_plans and the default weights 1/2, u(x, t) for u_t(x, 0) = 0."""
+    x = plus._dev_tensor(x, "input")
+    out = torch.empty_like(x) if out is None else plus._dev_tensor(out, "out")
+    _check(lib().fio_apply_wave(plus._h, minus._h, x.data_ptr(), out.data_ptr(), x.shape[0], float(w_plus),
+                                float(w_minus), int(adjoint), _stream_ptr(stream)))
+    return out
 
 
 def peak_probe(kind: str) -> float:

@@ -64,6 +64,7 @@ def test_calls_on_null_plan_fail_cleanly(lib):
     for impl in (0, 1, 2, 3):  # every switch kernel id, including the tensor-memory one
         assert lib.fio_plan_set_switch(None, impl) == -1
     assert lib.fio_plan_set_tuning(None, 3, -1, -1) == -1
+    assert lib.fio_apply_wave(None, None, None, None, 1, ctypes.c_double(0.5), ctypes.c_double(0.5), 0, None) == -1
 
 
 def test_binding_has_no_cpu_path():

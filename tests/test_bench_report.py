@@ -41,3 +41,10 @@ def test_kernel_report(switch_impl):
 
 def test_tf32_peak_is_derived_from_the_bf16_figure():
     assert 500.0 < bench.TF32_PEAK_FROM_BF16 < 1200.0
+
+
+def test_wave_timing_reports_instead_of_raising():
+    # without a usable device the wave leg returns an error record; the headline line survives
+    args = types.SimpleNamespace(steps=1, warmup=0)
+    rec = bench.run_wave(args, "cpu", lambda x: x, 1)
+    assert set(rec) == {"error"} or rec.get("unit") == "outputs/s"
