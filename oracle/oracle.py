@@ -24,16 +24,18 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fio_oracle.c")
+_SRC3 = os.path.join(_HERE, "fio_oracle3.c")  # the three-dimensional form
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 LINEAR, ELLIPSE, CIRCLE, SEPARABLE = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
-    """Compile fio_oracle.c into liboracle.so (gcc, OpenMP) when missing or stale."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile fio_oracle.c and fio_oracle3.c into liboracle.so (gcc, OpenMP) when missing or stale."""
+    srcs = [_SRC, _SRC3]
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(x) for x in srcs):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -58,6 +60,11 @@ def _L():
         lib.orc_phi_k.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         lib.orc_phi_k.restype = ctypes.c_double
         lib.orc_cheb_nodes.argtypes = [ctypes.c_int, dp]
+        lib.orc3_spherical_map.argtypes = [ctypes.c_int] * 4 + [dp]
+        lib.orc3_theta_xp.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, dp]
+        lib.orc3_theta_xp.restype = ctypes.c_double
+        lib.orc3_direct.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp, ctypes.c_int, lp, vp]
+        lib.orc3_butterfly.argtypes = [ctypes.c_int] * 3 + [dp] + [ctypes.c_int] * 3 + [vp, vp]
         lib.orc_lagrange_row.argtypes = [ctypes.c_int, ctypes.c_double, dp]
         lib.orc_polar_map.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
         lib.orc_num_stages.argtypes = [ctypes.c_int] * 3
@@ -179,6 +186,45 @@ def butterfly_adjoint(N, q, phase_id, params, g, s=-1, lm=-1, e=2) -> np.ndarray
     if rc != 0:
         raise ValueError("oracle adjoint rejected N=%d q=%d s=%d lm=%d" % (N, q, s, lm))
     return out
+
+
+# ---------------------------------------------------------------- three dimensions
+# f[k1 + N/2, k2 + N/2, k3 + N/2] and u[i1, i2, i3] (N, N, N); phases 0 linear and 2 sphere
+# (lambda x.k + c(x)|k|, c = (a + m sin sin sin)/b; eq. ex3 is [3, 1, 4, 1]).
+SPHERE = 2
+
+
+def spherical3(N, k) -> np.ndarray:
+    """Spherical coordinates (p1, p2, p3) of a lattice frequency k (the 3D polar map)."""
+    p = np.zeros(3)
+    _L().orc3_spherical_map(N, int(k[0]), int(k[1]), int(k[2]), _dp(p))
+    return p
+
+
+def theta3(phase_id, params, N, x, p) -> float:
+    """Phi(x, kappa(p)) in three dimensions."""
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    return float(_L().orc3_theta_xp(phase_id, _dp(_prm(params)), N, _dp(xx), _dp(pp)))
+
+
+def direct3(N, phase_id, params, f, xi=None) -> np.ndarray:
+    """3D direct sum u(x) = sum_k e^{2 pi i Phi(x,k)} f(k) at flat indices xi = i1 N^2 + i2 N + i3."""
+    f = np.ascontiguousarray(f, dtype=np.complex128).reshape(N, N, N)
+    xi = np.arange(N ** 3, dtype=np.int64) if xi is None else np.ascontiguousarray(xi, dtype=np.int64)
+    u = np.zeros(len(xi), dtype=np.complex128)
+    _L().orc3_direct(N, phase_id, _dp(_prm(params)), f.ctypes.data, len(xi),
+                     xi.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), u.ctypes.data)
+    return u
+
+
+def butterfly3(N, q, phase_id, params, f, s=-1, lm=-1, e=1) -> np.ndarray:
+    """FP64 CPU butterfly in three dimensions (q^3 Chebyshev grids, 8 children per box)."""
+    f = np.ascontiguousarray(f, dtype=np.complex128).reshape(N, N, N)
+    u = np.zeros((N, N, N), dtype=np.complex128)
+    if _L().orc3_butterfly(N, q, phase_id, _dp(_prm(params)), s, lm, e, f.ctypes.data, u.ctypes.data) != 0:
+        raise ValueError("oracle 3D butterfly rejected N=%d q=%d s=%d lm=%d e=%d" % (N, q, s, lm, e))
+    return u
 
 
 def wave_params(a, m, b, t, sign) -> list:
