@@ -6,7 +6,8 @@
  * dimensions with a three-dimensional Chebyshev grid for the interpolation of
  * e^{2 pi i R^{AB}(x,k)}, and reports it for the phase of eq. ex3,
  *     Phi(x,k) = x.k + c(x)|k|,  c(x) = (3 + sin 2pi x1 sin 2pi x2 sin 2pi x3)/4   (Table 3).
- * This file is a plain FP64 statement of that method (forward apply), in the
+ * This file is a plain FP64 statement of that method (forward apply and its exact
+ * conjugate transpose, the adjoint butterfly), in the
  * same order and notation as the two-dimensional oracle (fio_oracle.c), for
  * the tests only.  It shares no code with the CUDA library, nor with the
  * two-dimensional oracle (the small helpers are restated here).
@@ -466,6 +467,237 @@ static void orc3_term(const orc3_bf *bf, const double complex *st, double comple
   }
 }
 
+/* ---------------------------------------------------- adjoint butterfly */
+
+/* Conjugate transpose of the termination: for every A at level l1 and B at level s,
+ * d_t = e^{2 pi i theta(x^A_t,p0B)} sum_{x in A} L^A_t(x) e^{-2 pi i theta(x,p0B)} g(x). */
+static void orc3_adj_term(const orc3_bf *bf, const double complex *g, double complex *st) {
+  int N = bf->N, q = bf->q, q3 = bf->q3, l = bf->l1, lb = bf->L - l;
+  long nA = 1L << (3 * l), nB = orc3_nb(bf, lb);
+  int m = N >> l, m3 = m * m * m;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long a = 0; a < nA; a++) {
+    int ad[3];
+    double x0[3];
+    orc3_adec(l, a, ad);
+    orc3_xc(l, ad, x0);
+    double complex *v = malloc(sizeof(double complex) * m3);
+    double *w = malloc(sizeof(double) * 3 * m * q);  /* w[d][m_d][i] = L_i of the local offset m_d */
+    for (int d = 0; d < 3; d++)
+      for (int md = 0; md < m; md++)
+        for (int i = 0; i < q; i++)
+          w[(d * m + md) * q + i] = orc3_lag(q, bf->z, i, ((double)(ad[d] * m + md) / N - x0[d]) * (1 << l));
+    for (long b = 0; b < nB; b++) {
+      int bd[3];
+      double p0[3];
+      orc3_bdec(bf, lb, b, bd);
+      orc3_pc(bf, lb, bd, p0);
+      /* e^{-2 pi i theta(x,p0B)} g(x) for the grid points x of A */
+      for (int j = 0; j < m3; j++) {
+        int id[3] = {ad[0] * m + j / (m * m), ad[1] * m + (j / m) % m, ad[2] * m + j % m};
+        double x[3] = {(double)id[0] / N, (double)id[1] / N, (double)id[2] / N};
+        v[j] = conj(orc3_expi(orc3_theta(&bf->ph, x, p0))) * g[((long)id[0] * N + id[1]) * N + id[2]];
+      }
+      for (int t = 0; t < q3; t++) {
+        int td[3] = {t / (q * q), (t / q) % q, t % q};
+        double complex acc = 0;
+        for (int j = 0; j < m3; j++) {
+          int md[3] = {j / (m * m), (j / m) % m, j % m};
+          acc += w[(0 * m + md[0]) * q + td[0]] * w[(1 * m + md[1]) * q + td[1]] * w[(2 * m + md[2]) * q + td[2]] * v[j];
+        }
+        double xt[3];
+        orc3_xn(bf, l, ad, t, xt);
+        st[orc3_idx(bf, l, a, b, t)] = orc3_expi(orc3_theta(&bf->ph, xt, p0)) * acc;
+      }
+    }
+    free(v);
+    free(w);
+  }
+}
+
+/* Conjugate transpose of the x-recursion at level l (l -> l-1):
+ * d^{Ap Bc}_u = e^{2 pi i theta(x^{Ap}_u,p0Bc)} sum_{A in Ap} sum_t L^{Ap}_u(x^A_t) e^{-2 pi i theta(x^A_t,p0Bc)} d^{AB}_t. */
+static void orc3_adj_x(const orc3_bf *bf, int l, const double complex *in, double complex *out) {
+  int q3 = bf->q3, lb = bf->L - l;
+  long nAp = 1L << (3 * (l - 1)), nBc = orc3_nb(bf, lb + 1);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long ap = 0; ap < nAp; ap++) {
+    int apd[3];
+    orc3_adec(l - 1, ap, apd);
+    double complex *v = malloc(sizeof(double complex) * 8 * q3);
+    for (long bc = 0; bc < nBc; bc++) {
+      int cd[3], bd[3];
+      double pc[3];
+      orc3_bdec(bf, lb + 1, bc, cd);
+      for (int d = 0; d < 3; d++) bd[d] = cd[d] / 2;
+      long b = orc3_benc(bf, lb, bd);
+      orc3_pc(bf, lb + 1, cd, pc);
+      /* e^{-2 pi i theta(x^A_t,p0Bc)} d^{AB}_t for the eight children A of Ap */
+      for (int sg = 0; sg < 8; sg++) {
+        int ad[3] = {2 * apd[0] + (sg >> 2), 2 * apd[1] + ((sg >> 1) & 1), 2 * apd[2] + (sg & 1)};
+        long a = orc3_aenc(l, ad);
+        for (int t = 0; t < q3; t++) {
+          double xt[3];
+          orc3_xn(bf, l, ad, t, xt);
+          v[sg * q3 + t] = conj(orc3_expi(orc3_theta(&bf->ph, xt, pc))) * in[orc3_idx(bf, l, a, b, t)];
+        }
+      }
+      for (int u = 0; u < q3; u++) {
+        double complex acc = 0;
+        for (int sg = 0; sg < 8; sg++)
+          for (int t = 0; t < q3; t++) acc += bf->lag3[((long)sg * q3 + u) * q3 + t] * v[sg * q3 + t];
+        double xu[3];
+        orc3_xn(bf, l - 1, apd, u, xu);
+        out[orc3_idx(bf, l - 1, ap, bc, u)] = orc3_expi(orc3_theta(&bf->ph, xu, pc)) * acc;
+      }
+    }
+    free(v);
+  }
+}
+
+/* Conjugate transpose of the switch: d_u = sum_t e^{-2 pi i theta(x^A_t,p^B_u)} d_t. */
+static void orc3_adj_switch(const orc3_bf *bf, const double complex *in, double complex *out) {
+  int q3 = bf->q3, l = bf->lm, lb = bf->L - l;
+  long nA = 1L << (3 * l), nB = orc3_nb(bf, lb);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long a = 0; a < nA; a++) {
+    int ad[3];
+    orc3_adec(l, a, ad);
+    for (long b = 0; b < nB; b++) {
+      int bd[3];
+      orc3_bdec(bf, lb, b, bd);
+      for (int u = 0; u < q3; u++) {
+        double pu[3];
+        orc3_pn(bf, lb, bd, u, pu);
+        double complex acc = 0;
+        for (int t = 0; t < q3; t++) {
+          double xt[3];
+          orc3_xn(bf, l, ad, t, xt);
+          acc += conj(orc3_expi(orc3_theta(&bf->ph, xt, pu))) * in[orc3_idx(bf, l, a, b, t)];
+        }
+        out[orc3_idx(bf, l, a, b, u)] = acc;
+      }
+    }
+  }
+}
+
+/* Conjugate transpose of the p-recursion at level l (l -> l-1):
+ * d^{Ap Bc}_u = sum_{A in Ap} e^{-2 pi i theta(x0A,p^{Bc}_u)} sum_t L^B_t(p^{Bc}_u) e^{2 pi i theta(x0A,p^B_t)} d^{AB}_t. */
+static void orc3_adj_p(const orc3_bf *bf, int l, const double complex *in, double complex *out) {
+  int q3 = bf->q3, lb = bf->L - l;
+  long nAp = 1L << (3 * (l - 1)), nB = orc3_nb(bf, lb);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long ap = 0; ap < nAp; ap++) {
+    int apd[3];
+    orc3_adec(l - 1, ap, apd);
+    double complex *v = malloc(sizeof(double complex) * 8 * q3);
+    for (long b = 0; b < nB; b++) {
+      int bd[3];
+      orc3_bdec(bf, lb, b, bd);
+      double x0s[8][3];
+      /* e^{2 pi i theta(x0A,p^B_t)} d^{AB}_t for the eight children A of Ap */
+      for (int sg = 0; sg < 8; sg++) {
+        int ad[3] = {2 * apd[0] + (sg >> 2), 2 * apd[1] + ((sg >> 1) & 1), 2 * apd[2] + (sg & 1)};
+        long a = orc3_aenc(l, ad);
+        orc3_xc(l, ad, x0s[sg]);
+        for (int t = 0; t < q3; t++) {
+          double pt[3];
+          orc3_pn(bf, lb, bd, t, pt);
+          v[sg * q3 + t] = orc3_expi(orc3_theta(&bf->ph, x0s[sg], pt)) * in[orc3_idx(bf, l, a, b, t)];
+        }
+      }
+      for (int c = 0; c < 8; c++) {
+        int cd[3] = {2 * bd[0] + (c >> 2), 2 * bd[1] + ((c >> 1) & 1), 2 * bd[2] + (c & 1)};
+        long bc = orc3_benc(bf, lb + 1, cd);
+        for (int u = 0; u < q3; u++) {
+          double pu[3];
+          orc3_pn(bf, lb + 1, cd, u, pu);
+          double complex acc = 0;
+          for (int sg = 0; sg < 8; sg++) {
+            double complex part = 0;
+            /* L^B_t(p^{Bc}_u) */
+            for (int t = 0; t < q3; t++) part += bf->lag3[((long)c * q3 + t) * q3 + u] * v[sg * q3 + t];
+            acc += conj(orc3_expi(orc3_theta(&bf->ph, x0s[sg], pu))) * part;
+          }
+          out[orc3_idx(bf, l - 1, ap, bc, u)] = acc;
+        }
+      }
+    }
+    free(v);
+  }
+}
+
+/* Conjugate transpose of the initialization:
+ * fbar(k) = sum_{A at l0} e^{-2 pi i Phi(x0A,k)} sum_t L^B_t(p(k)) e^{2 pi i theta(x0A,p^B_t)} d^{AB}_t,
+ * B the box of p(k) at level L-l0. */
+static void orc3_adj_init(const orc3_bf *bf, const double complex *st, double complex *fbar) {
+  int N = bf->N, q = bf->q, q3 = bf->q3, l = bf->l0, lb = bf->L - l;
+  long nA = 1L << (3 * l), nB = orc3_nb(bf, lb), n3 = (long)N * N * N;
+  /* v^{AB}_t = e^{2 pi i theta(x0A,p^B_t)} d^{AB}_t */
+  double complex *v = malloc(sizeof(double complex) * nA * nB * q3);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long a = 0; a < nA; a++) {
+    int ad[3];
+    double x0[3];
+    orc3_adec(l, a, ad);
+    orc3_xc(l, ad, x0);
+    for (long b = 0; b < nB; b++) {
+      int bd[3];
+      orc3_bdec(bf, lb, b, bd);
+      for (int t = 0; t < q3; t++) {
+        double pt[3];
+        orc3_pn(bf, lb, bd, t, pt);
+        long i = orc3_idx(bf, l, a, b, t);
+        v[i] = orc3_expi(orc3_theta(&bf->ph, x0, pt)) * st[i];
+      }
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long k = 0; k < n3; k++) {
+    double kk[3] = {(double)(k / ((long)N * N)) - N / 2, (double)((k / N) % N) - N / 2, (double)(k % N) - N / 2};
+    int bd[3] = {orc3_box(bf->sp[3 * k], lb), orc3_box(bf->sp[3 * k + 1], lb + bf->e),
+                 orc3_box(bf->sp[3 * k + 2], lb + bf->e)};
+    long b = orc3_benc(bf, lb, bd);
+    double p0[3];
+    orc3_pc(bf, lb, bd, p0);
+    double h[3] = {(bf->sp[3 * k] - p0[0]) * (1 << lb), (bf->sp[3 * k + 1] - p0[1]) * (1 << (lb + bf->e)),
+                   (bf->sp[3 * k + 2] - p0[2]) * (1 << (lb + bf->e))};
+    double w[3][ORC3_QMAX];
+    for (int d = 0; d < 3; d++)
+      for (int i = 0; i < q; i++) w[d][i] = orc3_lag(q, bf->z, i, h[d]);
+    double complex acc = 0;
+    for (long a = 0; a < nA; a++) {
+      int ad[3];
+      double x0[3];
+      orc3_adec(l, a, ad);
+      orc3_xc(l, ad, x0);
+      double complex part = 0;
+      for (int t = 0; t < q3; t++) part += w[0][t / (q * q)] * w[1][(t / q) % q] * w[2][t % q] * v[orc3_idx(bf, l, a, b, t)];
+      acc += conj(orc3_expi(orc3_phi(&bf->ph, x0, kk))) * part;
+    }
+    fbar[k] = acc;
+  }
+  free(v);
+}
+
+/* Adjoint direct sum: fbar(k) = sum_x e^{-2 pi i Phi(x,k)} g(x) at flat frequency indices ki. */
+void orc3_direct_adjoint(int N, int phase_id, const double *prm, const double complex *g, int nk, const long *ki,
+                         double complex *fbar) {
+  orc3_phase ph = {phase_id, N, {prm[0], prm[1], prm[2], prm[3]}};
+  long n3 = (long)N * N * N;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int j = 0; j < nk; j++) {
+    long k = ki[j];
+    double kk[3] = {(double)(k / ((long)N * N)) - N / 2, (double)((k / N) % N) - N / 2, (double)(k % N) - N / 2};
+    double complex acc = 0;
+    for (long x = 0; x < n3; x++) {
+      double xx[3] = {(double)(x / ((long)N * N)) / N, (double)((x / N) % N) / N, (double)(x % N) / N};
+      acc += conj(orc3_expi(orc3_phi(&ph, xx, kk))) * g[x];
+    }
+    fbar[j] = acc;
+  }
+}
+
 /*
  * Forward 3D butterfly: f, u are N^3 complex (layout of orc3_direct).  s: truncation
  * depth (-1 = 3, at most floor(L/2)); lm: switch level (-1 = floor(L/2)); e: angular
@@ -503,6 +735,45 @@ int orc3_butterfly(int N, int q, int phase_id, const double *prm, int s, int lm,
     b = t;
   }
   orc3_term(&bf, a, u);
+  free(a);
+  free(b);
+  orc3_bf_free(&bf);
+  return 0;
+}
+
+/* Adjoint 3D butterfly: fbar = B^H g, the exact conjugate transpose of orc3_butterfly. */
+int orc3_butterfly_adjoint(int N, int q, int phase_id, const double *prm, int s, int lm, int e,
+                           const double complex *g, double complex *fbar) {
+  orc3_bf bf;
+  if (orc3_bf_init(&bf, N, q, phase_id, prm, s, lm, e)) return -1;
+  long sz = ((long)N * N * N << (2 * bf.e)) * bf.q3;
+  double complex *a = malloc(sizeof(double complex) * sz), *b = malloc(sizeof(double complex) * sz);
+  if (!a || !b) {
+    free(a);
+    free(b);
+    orc3_bf_free(&bf);
+    return -1;
+  }
+  orc3_adj_term(&bf, g, a);
+  for (int l = bf.l1; l >= bf.lm + 1; l--) {
+    orc3_adj_x(&bf, l, a, b);
+    double complex *t = a;
+    a = b;
+    b = t;
+  }
+  orc3_adj_switch(&bf, a, b);
+  {
+    double complex *t = a;
+    a = b;
+    b = t;
+  }
+  for (int l = bf.lm; l >= bf.l0 + 1; l--) {
+    orc3_adj_p(&bf, l, a, b);
+    double complex *t = a;
+    a = b;
+    b = t;
+  }
+  orc3_adj_init(&bf, a, fbar);
   free(a);
   free(b);
   orc3_bf_free(&bf);

@@ -65,6 +65,8 @@ def _L():
         lib.orc3_theta_xp.restype = ctypes.c_double
         lib.orc3_direct.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp, ctypes.c_int, lp, vp]
         lib.orc3_butterfly.argtypes = [ctypes.c_int] * 3 + [dp] + [ctypes.c_int] * 3 + [vp, vp]
+        lib.orc3_butterfly_adjoint.argtypes = [ctypes.c_int] * 3 + [dp] + [ctypes.c_int] * 3 + [vp, vp]
+        lib.orc3_direct_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp, ctypes.c_int, lp, vp]
         lib.orc_lagrange_row.argtypes = [ctypes.c_int, ctypes.c_double, dp]
         lib.orc_polar_map.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
         lib.orc_num_stages.argtypes = [ctypes.c_int] * 3
@@ -225,6 +227,25 @@ def butterfly3(N, q, phase_id, params, f, s=-1, lm=-1, e=1) -> np.ndarray:
     if _L().orc3_butterfly(N, q, phase_id, _dp(_prm(params)), s, lm, e, f.ctypes.data, u.ctypes.data) != 0:
         raise ValueError("oracle 3D butterfly rejected N=%d q=%d s=%d lm=%d e=%d" % (N, q, s, lm, e))
     return u
+
+
+def direct3_adjoint(N, phase_id, params, g, ki=None) -> np.ndarray:
+    """3D adjoint direct sum fbar(k) = sum_x e^{-2 pi i Phi(x,k)} g(x) at flat indices ki."""
+    g = np.ascontiguousarray(g, dtype=np.complex128).reshape(N, N, N)
+    ki = np.arange(N ** 3, dtype=np.int64) if ki is None else np.ascontiguousarray(ki, dtype=np.int64)
+    out = np.zeros(len(ki), dtype=np.complex128)
+    _L().orc3_direct_adjoint(N, phase_id, _dp(_prm(params)), g.ctypes.data, len(ki),
+                             ki.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), out.ctypes.data)
+    return out
+
+
+def butterfly3_adjoint(N, q, phase_id, params, g, s=-1, lm=-1, e=1) -> np.ndarray:
+    """The exact conjugate transpose of butterfly3."""
+    g = np.ascontiguousarray(g, dtype=np.complex128).reshape(N, N, N)
+    fb = np.zeros((N, N, N), dtype=np.complex128)
+    if _L().orc3_butterfly_adjoint(N, q, phase_id, _dp(_prm(params)), s, lm, e, g.ctypes.data, fb.ctypes.data) != 0:
+        raise ValueError("oracle 3D adjoint butterfly rejected N=%d q=%d s=%d lm=%d e=%d" % (N, q, s, lm, e))
+    return fb
 
 
 def wave_params(a, m, b, t, sign) -> list:

@@ -88,6 +88,35 @@ def test_butterfly3_accuracy_matches_table3(oracle):
         assert eps / 2 < err < 2 * eps, (err, eps)
 
 
+def test_direct3_adjoint_linear_phase_is_a_forward_dft(oracle):
+    # fbar(k) = sum_x e^{-2 pi i x.k} g(x) with x = i/N, k = m - N/2: e^{pi i (i1+i2+i3)}
+    # times numpy's forward FFT kernel, i.e. the FFT of (-1)^(i1+i2+i3) g
+    N = 8
+    g = sources3(N, 36)
+    fb = oracle.direct3_adjoint(N, 0, [], g).reshape(N, N, N)
+    i = np.arange(N)
+    sign = (-1.0) ** (i[:, None, None] + i[None, :, None] + i[None, None, :])
+    assert oracle.rel_l2(fb, np.fft.fftn(sign * g)) < 1e-12
+
+
+@pytest.mark.parametrize("N,q,s,e", [(8, 3, 0, 1), (8, 5, 1, 0), (16, 3, 0, 1)])
+def test_butterfly3_dot_test(oracle, N, q, s, e):
+    # <g, B f> = <B^H g, f> to rounding: the adjoint is the exact conjugate transpose
+    f, g = sources3(N, 37), sources3(N, 38)
+    a = np.vdot(g, oracle.butterfly3(N, q, oracle.SPHERE, EX3, f, s=s, e=e))
+    b = np.vdot(oracle.butterfly3_adjoint(N, q, oracle.SPHERE, EX3, g, s=s, e=e), f)
+    assert abs(a - b) < 1e-12 * abs(a)
+
+
+def test_butterfly3_adjoint_approximates_the_adjoint_sum(oracle):
+    # the adjoint butterfly approximates the adjoint direct sum as the forward does the forward
+    N, q = 8, 7
+    g = sources3(N, 39)
+    fb = oracle.butterfly3_adjoint(N, q, oracle.SPHERE, EX3, g, s=0, e=1)
+    ref = oracle.direct3_adjoint(N, oracle.SPHERE, EX3, g).reshape(N, N, N)
+    assert oracle.rel_l2(fb, ref) < 1e-2
+
+
 def test_butterfly3_rejects_bad_arguments(oracle):
     f = np.zeros((8, 8, 8), dtype=np.complex128)
     with pytest.raises(ValueError):
