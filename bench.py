@@ -118,7 +118,7 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) per launch at the N=1024, q=9, 32-RHS workload, from ncu captures of
-# the current kernels on smaller cases scaled by pairs x RHS (profiles/dram_traffic_small_cases.md).
+# the current kernels on smaller cases (inputs larger than L2), scaled by pairs x RHS.
 MEASURED_TRAFFIC = {"switch": 171.0e9, "trans_p": 172.3e9, "trans_x": 172.4e9, "init": 86.7e9, "term": 87.2e9}
 
 
@@ -147,47 +147,98 @@ def kernel_flops_bytes(kind: str, info, nrhs: int) -> tuple[float, float]:
     return 0.0, 0.0
 
 
-def kernel_report(prof: dict, info, steps: int, ms_step: float, switch_impl: int) -> tuple[dict, dict]:
-    """Per-kernel breakdown of one timed apply and the dominant kernel's roofline.
+def _tensor_switch(kind: str, switch_impl: int) -> bool:
+    return kind.startswith("switch") and switch_impl in (1, 3)
+
+
+def kernel_report(prof: dict, info, steps: int, switch_impl: int) -> tuple[dict, dict]:
+    """Per-kernel breakdown of the timed applies and the dominant kernel's roofline.
 
     prof: {kernel kind: (launches, total ms)} over `steps` applies of the headline plan (`info`
-    its PlanInfo); ms_step: CUDA-event time of one apply.  The roofline also carries the whole
-    apply's algorithmic flops against the same FP32 peak and, for a tensor-core switch, the
-    split-TF32 MMA work the switch issues against the TF32 peak."""
+    its PlanInfo).  Each kernel's fraction is its algorithmic work per launch over its average
+    CUDA-event duration, against the peak of the pipe it runs on: the FP32 FMA peak, or for a
+    tensor-core switch the TF32 peak (8 q^4 flops per pair and RHS, the split-TF32 products
+    counted once)."""
     kernels = {}
     for k, (n, ms) in prof.items():
         fl, by = kernel_flops_bytes(k, info, NRHS)
         avg = ms / n
-        kernels[k] = {"launches": n, "ms_per_launch": avg, "share": None, "gflops": fl / (avg * 1e-3) / 1e9,
-                      "gbs": by / (avg * 1e-3) / 1e9, "dram_bytes_measured": MEASURED_TRAFFIC.get(k)}
+        tc = _tensor_switch(k, switch_impl)
+        peak = TF32_PEAK_FROM_BF16 * 1e12 if tc else FP32_PEAK
+        kernels[k] = {"launches": n, "ms_per_launch": round(avg, 3), "share": None,
+                      "tflops": round(fl / (avg * 1e-3) / 1e12, 2), "pipe": "tf32 tensor" if tc else "fp32 fma",
+                      "frac": round(fl / (avg * 1e-3) / peak, 3), "gbs": round(by / (avg * 1e-3) / 1e9, 1)}
     tot = sum(v["ms_per_launch"] * v["launches"] for v in kernels.values())
     for v in kernels.values():
-        v["share"] = v["ms_per_launch"] * v["launches"] / tot
+        v["share"] = round(v["ms_per_launch"] * v["launches"] / tot, 3)
     dom = max(kernels, key=lambda k: kernels[k]["share"])
     fl, by = kernel_flops_bytes(dom, info, NRHS)
-    dom_ms = kernels[dom]["ms_per_launch"]
-    roof = {"kernel": dom, "bound": "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12,
-            "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s", "frac": fl / (dom_ms * 1e-3) / FP32_PEAK,
+    dom_ms = prof[dom][1] / prof[dom][0]
+    tc = _tensor_switch(dom, switch_impl)
+    peak = TF32_PEAK_FROM_BF16 * 1e12 if tc else FP32_PEAK
+    roof = {"kernel": dom, "bound": "tensor" if tc else "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12,
+            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": fl / (dom_ms * 1e-3) / peak,
             "traffic": MEASURED_TRAFFIC.get(dom) if (info.N, info.q, NRHS) == (1024, 9, 32) else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on a smaller "
                               "case, scaled by pairs x RHS",
-            "peak_source": FP32_PEAK_NOTE + " (derived, not measured)",
+            "peak_source": ("measured bf16 burst x nominal TF32/BF16 1.1/2.25 (of measured)" if tc
+                            else FP32_PEAK_NOTE + " (derived, not measured)"),
             "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
             "hbm_achieved_gbs": by / (dom_ms * 1e-3) / 1e9}
-    # the whole apply against the same FP32 roofline: all kernels' algorithmic flops per step
-    apply_fl = sum(kernel_flops_bytes(k, info, NRHS)[0] * v["launches"] for k, v in kernels.items()) / steps
-    roof["apply_achieved"] = apply_fl / (ms_step * 1e-3) / 1e12
-    roof["apply_frac"] = apply_fl / (ms_step * 1e-3) / FP32_PEAK
-    if switch_impl in (1, 3) and "switch" in kernels:
-        # tensor-core switch: the MMA work it issues (M = 128 rows, N = 64, K = 2q^2 rounded up to 8,
-        # 5 split-TF32 products per pair) against the TF32 peak (measured bf16 x the nominal 1.1 / 2.25)
-        kp = (2 * info.q * info.q + 7) // 8 * 8
-        tc_fl = 5 * 2 * 128 * 64 * kp * info.pairs_per_level * ((NRHS + 31) // 32)
-        tf32_peak = TF32_PEAK_FROM_BF16 * 1e12
-        sw = kernels["switch"]
-        sw["tensor_tflops"] = tc_fl / (sw["ms_per_launch"] * 1e-3) / 1e12
-        sw["tensor_frac_of_tf32_peak"] = tc_fl / (sw["ms_per_launch"] * 1e-3) / tf32_peak
     return kernels, roof
+
+
+def _hbm_peak_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def apply_roofline(info, nrhs: int, ms_apply: float, probes: dict) -> dict:
+    """The whole apply against its roofline time
+        T_roof = max(B_min / BW, F32 / P_fp32, F64 / P_fp64, 2E / P_mufu, F_tc / P_tf32)
+    with this plan's algorithmic counts (P = 2^e N^2 pairs per level, R RHS, M = 2^s):
+      F32  FP32 flops of the initialization, every translation level and the termination
+           (kernel_flops_bytes; the switch is not in it: it runs on the tensor cores);
+      F_tc the switch's complex MACs, 8 q^4 flops per pair and RHS, split-TF32 counted once;
+      E    phase evaluations e^{2 pi i theta}: q^4 per switch pair, 5 q^2 per pair of every
+           translation level, 4^s N^2 + q^2 P in the initialization, (q^2 + M^2) P in the
+           termination, each one sine and one cosine (2E special-function operations);
+      F64  FP64 flops: none in this build's FP32 form (its phases run in double-float on the
+           FP32 pipe); with FP64 phases at ~10 FP64 flops per evaluation the term is
+           reported separately as t_fp64_phases_ms;
+      B_min f in, u out and one state round trip at the switch: 2 N^2 R 8 + 2 P R q^2 8 bytes.
+    apply_frac = T_roof / t_apply."""
+    q, M, N, P, R = info.q, 1 << info.s, info.N, info.pairs_per_level, nrhs
+    ntrans = (info.lm - info.l0) + (info.l1 - info.lm)
+    f_init = kernel_flops_bytes("init", info, R)[0]
+    f_tr = kernel_flops_bytes("trans", info, R)[0]
+    f_term = kernel_flops_bytes("term", info, R)[0]
+    F32 = f_init + ntrans * f_tr + f_term
+    Ftc = 8 * q ** 4 * P * R
+    E = q ** 4 * P + ntrans * 5 * q * q * P + (4 ** info.s) * N * N + q * q * P + (q * q + M * M) * P
+    B = 2 * N * N * R * 8 + 2 * P * R * q * q * 8
+    p32 = FP32_PEAK
+    p64 = probes.get("fp64") if isinstance(probes.get("fp64"), float) else 1.06e12
+    pmufu = probes.get("sfu") if isinstance(probes.get("sfu"), float) else 4.9e12
+    ptf32 = TF32_PEAK_FROM_BF16 * 1e12
+    bw = _hbm_peak_gbs() * 1e9
+    terms = {"hbm_ms": B / bw * 1e3, "fp32_ms": F32 / p32 * 1e3, "tf32_ms": Ftc / ptf32 * 1e3,
+             "mufu_ms": 2 * E / pmufu * 1e3, "fp64_ms": 0.0}
+    t_roof = max(terms.values())
+    t64 = 10.0 * E / p64 * 1e3
+    return {"formula": "max(B_min/BW, F32/P_fp32, F64/P_fp64, 2E/P_mufu, F_tc/P_tf32)",
+            "F32": F32, "F_tc": Ftc, "E": E, "B_min": B, "F64": 0.0,
+            "terms_ms": {k: round(v, 2) for k, v in terms.items()}, "t_roof_ms": round(t_roof, 2),
+            "t_apply_ms": round(ms_apply, 2), "apply_frac": round(t_roof / ms_apply, 4),
+            "t_fp64_phases_ms": round(t64, 1),
+            "apply_frac_with_fp64_phases": round(max(t_roof, t64) / ms_apply, 4),
+            "peaks": {"fp32_tflops": round(p32 / 1e12, 2), "fp32_source": "derived (152 x 128 x 2 x 2.07 GHz)",
+                      "tf32_tflops": round(ptf32 / 1e12, 1), "tf32_source": "measured bf16 x 1.1/2.25 (of measured)",
+                      "hbm_gbs": round(bw / 1e9, 1), "hbm_source": "MEASURED_PEAKS.json (of measured)",
+                      "mufu_per_s": pmufu, "fp64_flops": p64, "mufu_fp64_source": "fio_peak_probe on this GPU"}}
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -235,6 +286,27 @@ def cpu_baseline(f0: np.ndarray, nsample: int):
            "sample": "FP64 direct sum (eq. dfio) at %d seeded x of RHS 0 of the N=%d workload, %.1f s wall"
                      % (nsample, N, dt)}
     return rec, xi, ref
+
+
+def cpu_butterfly_baseline():
+    """The FP64 CPU butterfly of the oracle (the paper's algorithm, step by step, dense 2D
+    Lagrange matrices), one RHS of the workload's phase, q, s and e, on all host threads and
+    on one.  The full N = 1024 runs for tens of minutes, so the bounded samples are N = 256
+    (all threads) and N = 128 (one thread); outputs/s = N^2 / wall time."""
+    from oracle import oracle as O
+    from paper_0809_0719_gb300.inputs import gaussian_sources
+
+    nthreads = O.threads()
+    rec = {"kind": "oracle", "q": Q, "s": S, "e": E, "nrhs": 1, "nproc": os.cpu_count()}
+    for key, n, th in (("all_cores", 256, nthreads), ("one_core", 128, 1)):
+        O.set_threads(th)
+        f = gaussian_sources(n, 0)
+        t0 = time.perf_counter()
+        O.butterfly(n, Q, O.ELLIPSE, list(PARAMS), f, s=S, e=E)
+        dt = time.perf_counter() - t0
+        rec[key] = {"N": n, "cores": th, "seconds": round(dt, 2), "value": n * n / dt, "unit": "outputs/s"}
+    O.set_threads(nthreads)
+    return rec
 
 
 def rel_err(u, xi, ref):
@@ -362,8 +434,8 @@ def run_ours(args, rank, world, dist):
     plan64 = fio.Plan(N, Q, "ellipse", PARAMS, "f64", nrhs_max=1, s=S, e=E)
     f64 = torch.from_numpy(F[:1]).to(dev)
     u64 = torch.empty_like(f64)
-    ms64 = tmax(time_steps(lambda: plan64.apply(f64, out=u64), max(1, args.steps // 2), max(3, args.warmup // 2),
-                           torch))
+    # a side measurement (5 s per apply): a few timed applies after one warm-up
+    ms64 = tmax(time_steps(lambda: plan64.apply(f64, out=u64), max(1, min(3, args.steps // 2)), 1, torch))
     u64h = u64[0].cpu().numpy()
     plan64.close()
     del f64, u64
@@ -380,15 +452,17 @@ def run_ours(args, rank, world, dist):
     out32 = whole_job_rate(N * N * NRHS, ms32, world)
     out64 = whole_job_rate(N * N, ms64, world)
 
-    kernels, roof = kernel_report(prof, info, args.steps, ms32, switch_impl)
+    kernels, roof = kernel_report(prof, info, args.steps, switch_impl)
     probes = {}
     for kind in ("fp32", "fp64", "sfu"):
         try:
             probes[kind] = fio.peak_probe(kind)
         except Exception as ex:  # measurement aid only
             probes[kind] = str(ex)
+    roof["apply"] = apply_roofline(info, NRHS, ms32, probes)
 
     base, xi, ref = cpu_baseline(F[0], NSAMPLE)
+    base["butterfly"] = cpu_butterfly_baseline()
     err32 = rel_err(u32, xi, ref)
     err64 = rel_err(u64h, xi, ref)
     line = {
@@ -396,30 +470,33 @@ def run_ours(args, rank, world, dist):
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (white-noise complex64 sources, seeds 0..31)",
         "config": dict(workload_config(), parallelism="replicas" if world > 1 else "single GPU"),
-        "rel_l2_err": err32,
-        "fp64_form": {"value": out64, "unit": "outputs/s", "ms_per_step": ms64, "nrhs": 1, "dtype": "f64",
-                      "rel_l2_err": err64},
-        "speedup_f32_vs_f64_form": out32 / out64,
-        "adjoint": {"value": whole_job_rate(N * N * NRHS, ms_adj, world), "unit": "outputs/s", "ms_per_step": ms_adj,
-                    "what": "fio_apply_adjoint on the same plan (32 RHS)", "dot_test": dot},
-        "amplitude": {"value": whole_job_rate(N * N * na, ms_amp, world), "unit": "outputs/s", "ms_per_step": ms_amp,
-                      "what": "fio_apply_amplitude: %d inputs x %d separated amplitude terms (eq. allfio) as one "
-                              "32-RHS butterfly" % (na, nt)},
-        "accuracy_bar_met": err32 <= max(2 * err64, 1e-5),
         "e2e": {"value": whole_job_rate(N * N * NRHS, e2e_ms, world), "unit": "outputs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": N * N * NRHS * 8, "d2h_bytes_per_step": N * N * NRHS * 8,
                 "api": "fio_apply_host (pinned host buffers)"},
         "gpu_launches": launches_per_step * args.steps,
-        "switch_kernel": ["fp32_fma", "tcgen05_tf32_smem_a", "fp32_fma_warp_specialised", "tcgen05_tf32_tmem_a"][switch_impl] + " (plan autotuner)",
-        "translation_rhs_subtile": trans_rs,
-        "switch_rhs_tile": sw_tile,
-        "kernels": kernels,
-        "roofline": roof,
-        "peak_probes": probes,
-        "cpu_baseline": base,
         "clocks": clk.summary(),
+        "cpu_baseline": base,
+        "switch_kernel": ["fp32_fma", "tcgen05_tf32_smem_a", "fp32_fma_warp_specialised",
+                          "tcgen05_tf32_tmem_a"][switch_impl] + " (plan autotuner)",
+        "translation_rhs_subtile": trans_rs, "switch_rhs_tile": sw_tile,
+        "peak_probes": probes,
         "uneven_batch": ub,
         "wave": wave,
+        "amplitude": {"value": whole_job_rate(N * N * na, ms_amp, world), "unit": "outputs/s", "ms_per_step": ms_amp,
+                      "what": "fio_apply_amplitude: %d inputs x %d separated amplitude terms (eq. allfio) as one "
+                              "32-RHS butterfly" % (na, nt)},
+        "kernels": kernels,
+        "roofline": roof,
+        # accuracy last, so that the end of the line carries it
+        "adjoint": {"value": whole_job_rate(N * N * NRHS, ms_adj, world), "unit": "outputs/s", "ms_per_step": ms_adj,
+                    "what": "fio_apply_adjoint on the same plan (32 RHS)"},
+        "fp64_form": {"value": out64, "unit": "outputs/s", "ms_per_step": ms64, "nrhs": 1, "dtype": "f64",
+                      "rel_l2_err": err64},
+        "speedup_f32_vs_f64_form": out32 / out64,
+        "dot_test": dot,
+        "rel_l2_err": err32,
+        "accuracy_bar": "FP32 err <= max(2 x FP64-form err, 1e-5) on 512 seeded x vs the FP64 direct sum",
+        "accuracy_bar_met": err32 <= max(2 * err64, 1e-5),
     }
     print(json.dumps(line), flush=True)
 
@@ -505,7 +582,7 @@ def run_uneven_batch(args, dev, with_errors=True):
             p64.close()
             errs.append(float(np.linalg.norm(ys[i] - u) / np.linalg.norm(u)))
         rec["rel_l2_err_vs_fp64_butterfly"] = {"max": max(errs), "median": statistics.median(errs),
-                                               "per_plan": errs}
+                                               "plans": len(errs)}
     return rec
 
 

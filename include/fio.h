@@ -49,7 +49,7 @@ enum {
   FIO_EINVAL = -1,   /* an argument is out of range or a pointer is NULL */
   FIO_ENOMEM = -2,   /* a device or host allocation failed */
   FIO_ECUDA = -3,    /* a CUDA runtime call failed (message has the CUDA error) */
-  FIO_ETIMEOUT = -4, /* reserved: a bounded device-side wait expired */
+  FIO_ETIMEOUT = -4, /* a bounded device-side wait of a tensor-core kernel expired (fio_check) */
   FIO_EDEVICE = -5   /* no usable CUDA device */
 };
 
@@ -90,8 +90,19 @@ enum { FIO_PHASE_LINEAR = 0, FIO_PHASE_ELLIPSE = 1, FIO_PHASE_CIRCLE = 2, FIO_PH
 int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, int nparams, int precision,
              int nrhs_max, int s, int e);
 
-/* fio_destroy -- free a plan (waits for the device to finish with it). NULL is a no-op. */
+/* fio_destroy -- free a plan (waits for the device to finish with it). NULL is a no-op.
+ * Also drops every batch that fio_apply_batch built over this plan. */
 int fio_destroy(fio_plan_t plan);
+
+/*
+ * fio_workspace_bytes -- device bytes of the working state an apply with nrhs
+ * right-hand sides needs: two levels of expansion coefficients (Sec. 4: only two
+ * consecutive levels are ever live), 2 x 2^e N^2 pairs x nrhs x q^2 complex values.
+ * The plan allocates this for nrhs_max itself (it holds its state buffers for its
+ * lifetime); the figure tells a caller how much of its memory budget a plan of a
+ * given size takes.  0 for a NULL plan or nrhs < 1.
+ */
+size_t fio_workspace_bytes(fio_plan_t plan, int nrhs);
 
 /*
  * fio_apply -- u = B f for nrhs right-hand sides (Sec. 4, eqs. alg2a-alg2d).
@@ -270,12 +281,15 @@ int fio_peak_probe(int kind, double *per_second);
  * whose tables plus two levels of 2^e N^2 q^2 nrhs complex coefficients exceed
  * 8 MiB is rejected with FIO_EINVAL and a message naming both sizes.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
- * share the array, which keeps the last call's contents (every coefficient is
- * written before it is read, so nothing needs clearing): calls that overlap on
- * the GPU (other streams, other host threads' streams) race and must be
- * serialised by the caller.  The host side copies its tables from pageable
- * memory, which waits for earlier work on the stream.
+ * device current.  All calls share the array, which keeps the last call's
+ * contents (every coefficient is written before it is read, so nothing needs
+ * clearing): calls that overlap on the GPU (other streams, other host threads'
+ * streams) race and must be serialised by the caller.  The host side copies its
+ * tables from one static pageable image that the next call rebuilds, which waits
+ * for earlier work on the stream; for the same reason a call on a stream that is
+ * being captured returns FIO_EINVAL.  FIO_F32 runs the generic FP32 kernels (no
+ * double-float phase tables), so its results agree with fio_apply's FP32 plans
+ * within the FP32 tolerance, not bit for bit.
  */
 int fio_apply_noalloc(int N, int q, int phase_id, const double *params, int nparams, int precision, int s, int e,
                       const void *f, void *u, int nrhs, void *stream);
@@ -323,6 +337,25 @@ enum {
  * parallel graph branches.  Allocates a small device descriptor buffer.
  */
 int fio_batch_create(fio_batch_t *out, int nplans, const fio_plan_t *plans, const int *nrhs, int flags);
+
+/*
+ * fio_apply_batch -- u[i] = B_i f[i] for the nplans plans in one go, each with its own
+ * DEVICE input and output pointer (layout and dtype as fio_apply; complex64; 16-byte
+ * aligned; nrhs[i] right-hand sides, 1 <= nrhs[i] <= plan i's nrhs_max).
+ * fio_apply_batch_adjoint -- fbar[i] = B_i^H g[i] likewise.
+ * The first call for a given list of plans and nrhs builds a batch exactly as
+ * fio_batch_create(plans, nrhs, 0) does and keeps it (at most 8 such batches; the
+ * oldest is dropped, which synchronises the device); later calls with the same plans
+ * and counts reuse it: one small kernel records the nplans pointer pairs, then one
+ * graph launch runs every step, one persistent launch per step and q-group.  Results
+ * are bit-identical to fio_batch_apply on packed copies of the same data.  Same rules
+ * as fio_batch_apply: FIO_F32 plans only, one call at a time per set of plans, and
+ * fio_destroy of any of the plans drops the kept batch.  Enqueued on `stream`.
+ */
+int fio_apply_batch(fio_plan_t *plans, int nplans, const void *const *f, void *const *u, const int *nrhs,
+                    void *stream);
+int fio_apply_batch_adjoint(fio_plan_t *plans, int nplans, const void *const *g, void *const *fbar, const int *nrhs,
+                            void *stream);
 
 /* fio_batch_destroy -- free the batch (waits for the device). NULL is a no-op. */
 int fio_batch_destroy(fio_batch_t batch);

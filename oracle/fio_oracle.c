@@ -207,6 +207,34 @@ void orc_direct(int N, int phase_id, const double *prm, const double complex *f,
   }
 }
 
+/* The same direct sum for nrhs sources at once (f holds nrhs N x N arrays one after
+ * another; u[r * nx + j] is RHS r at xi[j]).  Each phase e^{2 pi i Phi(x,k)} is
+ * evaluated once and multiplied into every RHS; per RHS the terms are added in the
+ * order orc_direct adds them, so each result equals orc_direct's bit for bit. */
+void orc_direct_multi(int N, int phase_id, const double *prm, int nrhs, const double complex *f, int nx,
+                      const long *xi, double complex *u) {
+  orc_phase ph = {phase_id, N, {prm[0], prm[1], prm[2], prm[3]}};
+  const long NN = (long)N * N;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < nx; j++) {
+    int i1 = (int)(xi[j] / N), i2 = (int)(xi[j] % N);
+    double x1 = (double)i1 / N, x2 = (double)i2 / N;
+    double complex *acc = calloc((size_t)nrhs, sizeof(double complex));
+    double complex *row = malloc(sizeof(double complex) * (size_t)nrhs);
+    for (int a = 0; a < N; a++) {
+      for (int r = 0; r < nrhs; r++) row[r] = 0;
+      for (int b = 0; b < N; b++) {
+        const double complex e = orc_expi(orc_theta_k(&ph, x1, x2, a - N / 2, b - N / 2));
+        for (int r = 0; r < nrhs; r++) row[r] += e * f[r * NN + (long)a * N + b];
+      }
+      for (int r = 0; r < nrhs; r++) acc[r] += row[r];
+    }
+    for (int r = 0; r < nrhs; r++) u[(long)r * nx + j] = acc[r];
+    free(acc);
+    free(row);
+  }
+}
+
 /* Adjoint direct sum: fbar(k) = sum_{x in X} e^{-2 pi i Phi(x,k)} g(x), at the
  * flat frequency indices ki[j] = (k1+N/2)*N + (k2+N/2). */
 void orc_direct_adjoint(int N, int phase_id, const double *prm, const double complex *g, int nk, const long *ki,

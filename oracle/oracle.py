@@ -53,6 +53,7 @@ def _L():
         vp = ctypes.c_void_p
         lib.orc_direct.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp, ctypes.c_int, lp, vp]
         lib.orc_direct_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp, ctypes.c_int, lp, vp]
+        lib.orc_direct_multi.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, vp, ctypes.c_int, lp, vp]
         lib.orc_butterfly.argtypes = [ctypes.c_int] * 3 + [dp] + [ctypes.c_int] * 3 + [vp, vp, ctypes.c_int, vp]
         lib.orc_butterfly_adjoint.argtypes = [ctypes.c_int] * 3 + [dp] + [ctypes.c_int] * 3 + [vp, vp]
         lib.orc_theta_xp.argtypes = [ctypes.c_int, dp, ctypes.c_int] + [ctypes.c_double] * 4
@@ -134,6 +135,19 @@ def direct(N, phase_id, params, f, xi=None) -> np.ndarray:
     prm = _prm(params)
     _L().orc_direct(N, phase_id, _dp(prm), f.ctypes.data, len(xi),
                     xi.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), u.ctypes.data)
+    return u
+
+
+def direct_multi(N, phase_id, params, F, xi=None) -> np.ndarray:
+    """Direct sum of eq. dfio for every source array of F (R, N, N) at flat grid indices xi;
+    returns (R, len(xi)).  Each RHS equals direct() on it bit for bit (same order of terms);
+    the phases are evaluated once per (x, k) for all RHS."""
+    F = np.ascontiguousarray(F, dtype=np.complex128).reshape(-1, N, N)
+    xi = np.arange(N * N, dtype=np.int64) if xi is None else np.ascontiguousarray(xi, dtype=np.int64)
+    u = np.zeros((F.shape[0], len(xi)), dtype=np.complex128)
+    prm = _prm(params)
+    _L().orc_direct_multi(N, phase_id, _dp(prm), F.shape[0], F.ctypes.data, len(xi),
+                          xi.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), u.ctypes.data)
     return u
 
 

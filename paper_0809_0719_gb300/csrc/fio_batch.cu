@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
+#include <mutex>
 #include <cstring>
 #include <map>
 #include <new>
@@ -67,6 +68,27 @@ int batch_dispatch(const BLaunch &L, cudaStream_t st, int optin, int *blocks_per
 __global__ void k_batch_io(BIo *io, const float2 *in, float2 *out) {
   io->in = in;
   io->out = out;
+  io->pin = nullptr;
+  io->pout = nullptr;
+}
+
+// Per-plan user pointers of fio_apply_batch, passed by value in chunks of kPtrChunk plans.
+constexpr int kPtrChunk = 1024;
+struct PtrChunk {
+  const float2 *in[kPtrChunk];
+  float2 *out[kPtrChunk];
+};
+__global__ void k_batch_io_ptrs(BIo *io, const float2 **pin, float2 **pout, int first, int n, PtrChunk c) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    pin[first + i] = c.in[i];
+    pout[first + i] = c.out[i];
+  }
+  if (threadIdx.x == 0) {
+    io->in = nullptr;
+    io->out = nullptr;
+    io->pin = pin;
+    io->pout = pout;
+  }
 }
 
 struct Group {
@@ -96,6 +118,8 @@ struct fio_batch_s {
   std::vector<std::vector<HostLaunch>> sched[2];  // [fwd/adj][group] -> launches in order
   void *dev = nullptr;
   BIo *io = nullptr;
+  const float2 **pin = nullptr;  // device: per-plan user pointers (fio_apply_batch)
+  float2 **pout = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   int parallel = 1, tuned = 0;
   double tune_ms = 0.0;
@@ -171,6 +195,7 @@ int build_schedule(fio_batch_s *b, int adj) {
         w.g.rt = kRMax;
         w.g.U = 1;
         w.io_off = b->off[i];
+        w.plan = i;
         w.nrt = (b->nrhs[i] + kRMax - 1) / kRMax;
         float2 *S[2] = {(float2 *)d.state[0], (float2 *)d.state[1]};
         switch (kind) {
@@ -337,7 +362,38 @@ void destroy_batch(fio_batch_s *b) {
   delete b;
 }
 
+// Batches built by fio_apply_batch, keyed by the plans' serial numbers and the RHS
+// counts; an entry is dropped when one of its plans is destroyed.
+struct CachedBatch {
+  std::vector<unsigned long long> serials;
+  std::vector<int> nrhs;
+  fio_batch_s *b;
+};
+std::mutex g_cache_mu;
+std::vector<CachedBatch> g_cache;
+constexpr size_t kCacheMax = 8;
+
 }  // namespace
+
+namespace fio {
+void batch_cache_forget(fio_plan_t p) {
+  std::vector<fio_batch_s *> drop;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (size_t i = 0; i < g_cache.size();) {
+      bool has = false;
+      for (unsigned long long sn : g_cache[i].serials) has = has || sn == p->serial;
+      if (has) {
+        drop.push_back(g_cache[i].b);
+        g_cache.erase(g_cache.begin() + i);
+      } else {
+        i++;
+      }
+    }
+  }
+  for (fio_batch_s *b : drop) destroy_batch(b);
+}
+}  // namespace fio
 
 extern "C" {
 
@@ -388,18 +444,21 @@ int fio_batch_create(fio_batch_t *out, int nplans, const fio_plan_t *plans, cons
       destroy_batch(b);
       return rc;
     }
-  // one device buffer: io slot | items | start arrays
+  // one device buffer: io slot | items | start arrays | per-plan in and out pointers
   size_t nstart = 0;
   for (int adj = 0; adj < 2; adj++)
     for (auto &gl : b->sched[adj])
       for (HostLaunch &h : gl) nstart += h.L.n + 1;
   const size_t o_items = 256, o_start = (o_items + b->items.size() * sizeof(BWork) + 255) & ~(size_t)255;
-  const size_t bytes = o_start + nstart * sizeof(long long);
+  const size_t o_ptrs = (o_start + nstart * sizeof(long long) + 255) & ~(size_t)255;
+  const size_t bytes = o_ptrs + 2 * (size_t)b->nplans * sizeof(void *);
   if ((ce = cudaMalloc(&b->dev, bytes)) != cudaSuccess) {
     destroy_batch(b);
     return bcuda((int)ce, "cudaMalloc(batch descriptors)");
   }
   b->io = (BIo *)b->dev;
+  b->pin = (const float2 **)((char *)b->dev + o_ptrs);
+  b->pout = (float2 **)(b->pin + b->nplans);
   BWork *d_items = (BWork *)((char *)b->dev + o_items);
   long long *d_start = (long long *)((char *)b->dev + o_start);
   size_t si = 0;
@@ -549,6 +608,65 @@ int fio_batch_apply(fio_batch_t b, const void *in, void *out, int adjoint, void 
   if (rc) return rc;
   const cudaError_t ce = cudaGraphLaunch(b->exec[adjoint ? 1 : 0], st);
   return ce == cudaSuccess ? FIO_OK : bcuda((int)ce, "cudaGraphLaunch");
+}
+
+static int apply_batch_ptrs(fio_plan_t *plans, int nplans, const void *const *in, void *const *out,
+                            const int *nrhs, int adjoint, void *stream) {
+  if (!plans || !in || !out || !nrhs) return bfail(FIO_EINVAL, "NULL plans, data pointer arrays or nrhs");
+  if (nplans < 1 || nplans > 4096) return bfail(FIO_EINVAL, "nplans=%d outside [1, 4096]", nplans);
+  for (int i = 0; i < nplans; i++) {
+    if (!plans[i]) return bfail(FIO_EINVAL, "plan %d is NULL", i);
+    if (!in[i] || !out[i]) return bfail(FIO_EINVAL, "data pointer %d is NULL", i);
+    if (((uintptr_t)in[i] | (uintptr_t)out[i]) & 15) return bfail(FIO_EINVAL, "data pointers %d are not 16-byte aligned", i);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  fio_batch_s *b = nullptr;
+  for (CachedBatch &c : g_cache) {
+    if ((int)c.serials.size() != nplans) continue;
+    bool same = true;
+    for (int i = 0; i < nplans && same; i++) same = c.serials[i] == plans[i]->serial && c.nrhs[i] == nrhs[i];
+    if (same) b = c.b;
+  }
+  if (!b) {
+    int rc = fio_batch_create(&b, nplans, plans, nrhs, 0);
+    if (rc) return rc;
+    if (g_cache.size() >= kCacheMax) {
+      destroy_batch(g_cache.front().b);
+      g_cache.erase(g_cache.begin());
+    }
+    CachedBatch c;
+    for (int i = 0; i < nplans; i++) c.serials.push_back(plans[i]->serial);
+    c.nrhs.assign(nrhs, nrhs + nplans);
+    c.b = b;
+    g_cache.push_back(c);
+  }
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != b->device) return bfail(FIO_EINVAL, "plans were built on device %d but device %d is current", b->device, dev);
+  for (int first = 0; first < nplans; first += kPtrChunk) {
+    const int n = std::min(kPtrChunk, nplans - first);
+    PtrChunk c;
+    for (int i = 0; i < n; i++) {
+      c.in[i] = (const float2 *)in[first + i];
+      c.out[i] = (float2 *)out[first + i];
+    }
+    k_batch_io_ptrs<<<1, 256, 0, st>>>(b->io, b->pin, b->pout, first, n, c);
+  }
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return bcuda((int)ce, "batch pointer kernel");
+  ce = cudaGraphLaunch(b->exec[adjoint ? 1 : 0], st);
+  return ce == cudaSuccess ? FIO_OK : bcuda((int)ce, "cudaGraphLaunch");
+}
+
+int fio_apply_batch(fio_plan_t *plans, int nplans, const void *const *f, void *const *u, const int *nrhs,
+                    void *stream) {
+  return apply_batch_ptrs(plans, nplans, f, u, nrhs, 0, stream);
+}
+
+int fio_apply_batch_adjoint(fio_plan_t *plans, int nplans, const void *const *g, void *const *fbar, const int *nrhs,
+                            void *stream) {
+  return apply_batch_ptrs(plans, nplans, g, fbar, nrhs, 1, stream);
 }
 
 int fio_batch_info(fio_batch_t b, fio_batch_info_t *info) {

@@ -26,14 +26,24 @@ struct BWork {
   long long io_off;  // the plan's element offset in the packed user buffers
   int nrt;           // RHS tiles of kRMax per unit
   int maxsrc, GA;    // initialization only: sources per box, boxes A per pass
-  int pad_;
+  int plan;          // the plan's index in the batch
 };
-// The packed user buffers of the current apply, written by a one-thread kernel
-// ahead of each graph launch so that the captured graph needs no new pointers.
+// The user buffers of the current apply, written by a small kernel ahead of each
+// graph launch so that the captured graph needs no new pointers: either one packed
+// buffer per direction (pin, pout NULL; plan i at element io_off), or one pointer per
+// plan (pin[i], pout[i]: fio_apply_batch).
 struct BIo {
   const float2 *in;
   float2 *out;
+  const float2 *const *pin;
+  float2 *const *pout;
 };
+__device__ __forceinline__ const float2 *io_in(const BIo *io, const BWork &w) {
+  return io->pin ? io->pin[w.plan] : io->in + w.io_off;
+}
+__device__ __forceinline__ float2 *io_out(const BIo *io, const BWork &w) {
+  return io->pout ? io->pout[w.plan] : io->out + w.io_off;
+}
 
 // Item holding work index w: the largest i with start[i] <= w.
 __device__ __forceinline__ int batch_find(const long long *__restrict__ start, int n, long long w) {
@@ -90,9 +100,8 @@ __global__ void __launch_bounds__(InitShape<Q>::threads) kb_init(const BWork *__
                                                                   const long long *__restrict__ start, int n,
                                                                   const BIo *__restrict__ io) {
   __shared__ BWork w_s;
-  const float2 *base = io->in;
   batch_loop(items, start, n, w_s, [&](long long unit, int ry) {
-    k32_init_body<Q>(w_s.tb, w_s.tf, w_s.ph, w_s.g, w_s.maxsrc, w_s.GA, base + w_s.io_off, w_s.out, unit, ry);
+    k32_init_body<Q>(w_s.tb, w_s.tf, w_s.ph, w_s.g, w_s.maxsrc, w_s.GA, io_in(io, w_s), w_s.out, unit, ry);
   });
 }
 
@@ -100,9 +109,8 @@ template <int Q>
 __global__ void __launch_bounds__(256) kb_init_adj(const BWork *__restrict__ items, const long long *__restrict__ start,
                                                    int n, const BIo *__restrict__ io) {
   __shared__ BWork w_s;
-  float2 *base = io->out;
   batch_loop(items, start, n, w_s, [&](long long unit, int ry) {
-    k32_init_adj_body<Q>(w_s.tb, w_s.tf, w_s.ph, w_s.g, w_s.maxsrc, w_s.in, base + w_s.io_off, unit, ry);
+    k32_init_adj_body<Q>(w_s.tb, w_s.tf, w_s.ph, w_s.g, w_s.maxsrc, w_s.in, io_out(io, w_s), unit, ry);
   });
 }
 
@@ -111,9 +119,8 @@ __global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) kb_term(const 
                                                                          const long long *__restrict__ start, int n,
                                                                          VMat<float, Q> vm, const BIo *__restrict__ io) {
   __shared__ BWork w_s;
-  float2 *base = io->out;
   batch_loop(items, start, n, w_s, [&](long long unit, int ry) {
-    k32_term_body<Q>(w_s.tb, w_s.tf, w_s.ph, w_s.g, vm, w_s.in, base + w_s.io_off, unit, ry);
+    k32_term_body<Q>(w_s.tb, w_s.tf, w_s.ph, w_s.g, vm, w_s.in, io_out(io, w_s), unit, ry);
   });
 }
 
@@ -123,9 +130,8 @@ __global__ void __launch_bounds__(32 * (Q > kTermM ? Q : kTermM)) kb_term_adj(co
                                                                              VMat<float, Q> vm,
                                                                              const BIo *__restrict__ io) {
   __shared__ BWork w_s;
-  const float2 *base = io->in;
   batch_loop(items, start, n, w_s, [&](long long unit, int ry) {
-    k32_term_adj_body<Q>(w_s.tb, w_s.tf, w_s.ph, w_s.g, vm, base + w_s.io_off, w_s.out, unit, ry);
+    k32_term_adj_body<Q>(w_s.tb, w_s.tf, w_s.ph, w_s.g, vm, io_in(io, w_s), w_s.out, unit, ry);
   });
 }
 

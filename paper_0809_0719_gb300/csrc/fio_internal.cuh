@@ -10,6 +10,7 @@ struct fio_plan_s {
   long long table_bytes, state_bytes;
   void *stage_buf[2];
   size_t stage_bytes;
+  unsigned long long serial;  // unique per plan in this process (keys fio_apply_batch's cache)
 };
 
 namespace fio {
@@ -19,4 +20,5 @@ int run_q7(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, i
 int run_q9(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
 int run_q11(const PlanDev &, int, const void *, void *, int, cudaStream_t, int, int *);
 void set_last_error(const char *msg);
+void batch_cache_forget(fio_plan_t p);  // drop fio_apply_batch's batches that use p
 }  // namespace fio

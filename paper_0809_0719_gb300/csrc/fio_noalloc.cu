@@ -9,8 +9,12 @@
 // and source tables and the two level buffers of expansion coefficients -- in
 // one file-scope device array of fixed size, and builds the host side of the
 // tables in fixed-size static host buffers.  It calls no cudaMalloc, cudaFree
-// or allocating library routine.  The kernels and the level schedule are the
-// ones fio_apply uses.
+// or allocating library routine.  The level schedule is fio_apply's; the FP32
+// form runs the generic FP32 kernels (no double-float phase tables are built
+// here), which agree with fio_apply's FP32 plans within the FP32 tolerance, not
+// bit for bit.  The tables are copied from one static host image that the next
+// call rebuilds, so a call on a stream that is being captured is refused: a
+// replayed copy would read whatever the image holds at replay time.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -107,6 +111,10 @@ extern "C" int fio_apply_noalloc(int N, int q, int phase_id, const double *param
   if (nrhs < 1) return fail(FIO_EINVAL, "nrhs=%d must be >= 1", nrhs);
   if (!f || !u) return fail(FIO_EINVAL, "NULL data pointer");
   if (((uintptr_t)f | (uintptr_t)u) & 15) return fail(FIO_EINVAL, "data pointers must be 16-byte aligned");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return fail(FIO_EINVAL, "fio_apply_noalloc cannot run while its stream is being captured: it copies its tables "
+                            "from a host image that the next call rewrites");
 
   const long long NN = (long long)N * N;
   const int lb = L - s;

@@ -10,6 +10,7 @@
 //   * two state buffers (only two consecutive levels are ever live, Sec. 4).
 // The 1D translation matrices T^0, T^1 and the termination matrix V are
 // position- and level-independent (Sec. 4) and travel as kernel arguments.
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -137,6 +138,8 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   if (ce != cudaSuccess) return fail(FIO_EDEVICE, "no CUDA device: %s", cudaGetErrorString(ce));
 
   fio_plan_s *p = new (std::nothrow) fio_plan_s();
+  static std::atomic<unsigned long long> next_serial{1};
+  if (p) p->serial = next_serial++;
   if (!p) return fail(FIO_ENOMEM, "host allocation failed");
   p->device = dev;
   PlanDev &d = p->d;
@@ -378,8 +381,15 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   return FIO_OK;
 }
 
+size_t fio_workspace_bytes(fio_plan_t p, int nrhs) {
+  if (!p || nrhs < 1) return 0;
+  const size_t eb = p->d.precision == FIO_F32 ? 8 : 16;
+  return 2 * ((size_t)p->d.N * p->d.N << p->d.e) * (size_t)nrhs * p->d.q * p->d.q * eb;
+}
+
 int fio_destroy(fio_plan_t p) {
   if (!p) return FIO_OK;
+  fio::batch_cache_forget(p);
   cudaDeviceSynchronize();
   if (p->d.prof) {
     for (int i = 0; i < 2 * fio::kProfSlots; i++) cudaEventDestroy(p->d.prof->ev[i]);

@@ -88,6 +88,11 @@ def lib() -> ctypes.CDLL:
             L.fio_batch_apply.argtypes = [vp, vp, vp, ip, vp]
             L.fio_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
             L.fio_batch_profile.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(KernelTime), ip, ctypes.POINTER(ip)]
+            L.fio_apply_batch.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                          ctypes.POINTER(ip), vp]
+            L.fio_apply_batch_adjoint.argtypes = L.fio_apply_batch.argtypes
+            L.fio_workspace_bytes.argtypes = [vp, ip]
+            L.fio_workspace_bytes.restype = ctypes.c_size_t
             L.fio_last_error.restype = ctypes.c_char_p
             _lib = L
         return _lib
@@ -219,6 +224,10 @@ class Plan:
         """fio_check: synchronise and raise if a bounded device-side wait expired."""
         _check(lib().fio_check(self._h, _stream_ptr(stream)))
 
+    def workspace_bytes(self, nrhs: int) -> int:
+        """fio_workspace_bytes: device bytes of the two state levels for nrhs RHS."""
+        return int(lib().fio_workspace_bytes(self._h, int(nrhs)))
+
     def kernel_launches(self, nrhs: int, adjoint: bool = False) -> int:
         return int(lib().fio_kernel_launches(self._h, nrhs, int(adjoint)))
 
@@ -303,6 +312,25 @@ class Batch:
         """Per-plan (nrhs, N, N) views of a packed buffer."""
         return [packed[self.offsets[i]:self.offsets[i + 1]].view(self.nrhs[i], p.N, p.N)
                 for i, p in enumerate(self.plans)]
+
+
+def apply_batch(plans, xs, outs=None, adjoint: bool = False, stream=None):
+    """fio_apply_batch (adjoint: fio_apply_batch_adjoint): every FP32 plan i applied to its own
+    (nrhs_i, N_i, N_i) complex64 CUDA tensor xs[i] in one graph launch (the library keeps the
+    batch of these plans and counts for later calls).  Returns the list of outputs."""
+    plans = list(plans)
+    n = len(plans)
+    if len(xs) != n:
+        raise ValueError("one input per plan")
+    xs = [p._dev_tensor(x, "input %d" % i) for i, (p, x) in enumerate(zip(plans, xs))]
+    outs = [torch.empty_like(x) for x in xs] if outs is None else [p._dev_tensor(o, "out") for p, o in zip(plans, outs)]
+    ph = (ctypes.c_void_p * n)(*[p._h for p in plans])
+    pin = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    pout = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    nr = (ctypes.c_int * n)(*[x.shape[0] for x in xs])
+    fn = lib().fio_apply_batch_adjoint if adjoint else lib().fio_apply_batch
+    _check(fn(ph, n, pin, pout, nr, _stream_ptr(stream)))
+    return outs
 
 
 def plan_auto(N: int, target: float, phase="ellipse", params=(2.0, 1.0, 16.0, 1.0), precision="f32",

@@ -28,7 +28,10 @@ def lib():
 
 def test_header_declares_the_api():
     names = header_functions()
-    for n in ("fio_plan", "fio_apply", "fio_apply_adjoint", "fio_destroy", "fio_last_error"):
+    # the boundary's calls: plan, apply, adjoint, destroy, errors, the batch of uneven plans
+    # with one pointer per plan, and the workspace size
+    for n in ("fio_plan", "fio_apply", "fio_apply_adjoint", "fio_destroy", "fio_last_error", "fio_apply_batch",
+              "fio_apply_batch_adjoint", "fio_workspace_bytes"):
         assert n in names
 
 
@@ -55,6 +58,17 @@ def test_plan_rejects_bad_arguments_without_a_gpu(lib):
         rc = lib.fio_plan(ctypes.byref(h), N, q, ph, prm, npar, prec, nr, s, e)
         assert rc == -1, (N, q, ph, npar, prec, nr, s, e, rc)
         assert len(lib.fio_last_error()) > 0
+
+
+def test_batch_and_workspace_reject_bad_arguments_without_a_gpu(lib):
+    vp = ctypes.c_void_p
+    plans = (vp * 1)(None)
+    ptrs = (vp * 1)(None)
+    nr = (ctypes.c_int * 1)(1)
+    assert lib.fio_apply_batch(plans, 1, ptrs, ptrs, nr, None) == -1
+    assert lib.fio_apply_batch(None, 1, ptrs, ptrs, nr, None) == -1
+    assert lib.fio_apply_batch_adjoint(plans, 0, ptrs, ptrs, nr, None) == -1
+    assert lib.fio_workspace_bytes(None, 1) == 0
 
 
 def test_calls_on_null_plan_fail_cleanly(lib):

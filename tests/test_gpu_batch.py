@@ -163,3 +163,35 @@ def test_uneven_batch_dot_test(uneven):
         a, b = torch.vdot(g64, bf64), torch.vdot(bg64, f64)
         r = abs(a - b).item() / (g64.norm() * bf64.norm()).item()
         assert r < 1e-6, (i, r)
+
+
+def test_apply_batch_with_one_pointer_per_plan(fio):
+    # fio_apply_batch(plans, nplans, f[], u[], nrhs[], stream): each plan's own input and
+    # output pointer; bit-identical to each plan alone (FFMA switch), forward and adjoint,
+    # on repeated calls (the kept batch) and after a plan of the list is destroyed and the
+    # list rebuilt (the kept batch is dropped with it)
+    plans = _plans(fio, SMALL)
+    try:
+        for base, adj in ((4, False), (5, True), (6, False)):
+            xs = _sources(SMALL, base)
+            ys = fio.apply_batch(plans, xs, adjoint=adj)
+            torch.cuda.synchronize()
+            for i, p in enumerate(plans):
+                ref = p.adjoint(xs[i]) if adj else p.apply(xs[i])
+                assert torch.equal(ys[i], ref), (i, adj)
+        # drop one plan and rebuild it: the library's kept batch for the old list must go
+        plans[1].close()
+        N, q, phase, nrhs = SMALL[1]
+        plans[1] = fio.Plan(N, q, phase, PARAMS[phase], "f32", nrhs_max=nrhs)
+        plans[1].set_switch(0)
+        xs = _sources(SMALL, 7)
+        ys = fio.apply_batch(plans, xs)
+        torch.cuda.synchronize()
+        for i, p in enumerate(plans):
+            assert torch.equal(ys[i], p.apply(xs[i])), i
+        # the workspace figure is the two state levels of 2^e N^2 q^2 complex64 per RHS
+        p = plans[0]
+        assert p.workspace_bytes(2) == 2 * (p.N * p.N << p.info.e) * 2 * p.q * p.q * 8
+    finally:
+        for p in plans:
+            p.close()

@@ -84,6 +84,21 @@ def test_direct_adjoint_linear_phase_is_a_forward_dft(oracle, N):
     assert oracle.rel_l2(fb, ref) < 1e-12
 
 
+def test_direct_multi_rhs_is_a_dft_per_rhs_and_equals_single_sums(oracle):
+    # the multi-RHS direct sum: for the linear phase every RHS is the 2D DFT of its
+    # sources (closed form), and for the ellipse phase it reproduces the single-RHS
+    # sums bit for bit (the terms are added in the same order)
+    N = 16
+    F = np.stack([gaussian_sources(N, 40 + r) for r in range(3)])
+    U = oracle.direct_multi(N, oracle.LINEAR, [], F)
+    for r in range(3):
+        assert oracle.rel_l2(U[r].reshape(N, N), dft_of(F[r])) < 1e-12
+    xi = sample_indices(N, 40, 4)
+    U = oracle.direct_multi(N, oracle.ELLIPSE, ELL16, F, xi)
+    for r in range(3):
+        assert np.array_equal(U[r], oracle.direct(N, oracle.ELLIPSE, ELL16, F[r], xi))
+
+
 def test_direct_sample_matches_full(oracle):
     N = 32
     f = gaussian_sources(N, 14)

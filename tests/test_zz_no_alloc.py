@@ -79,3 +79,20 @@ def test_noalloc_rejects_problems_beyond_the_static_limit(lib):
     assert b"static limit" in lib.fio_last_error()
     rc = lib.fio_apply_noalloc(64, 5, 1, prm, 4, 0, 3, 2, f.data_ptr(), f.data_ptr(), 1, None)
     assert rc == -1
+
+
+def test_noalloc_takes_no_device_memory(lib):
+    # the property the entry point exists for: after one warm-up call (which looks up the
+    # static array's address), a call changes the device's free memory by nothing
+    N, q = 32, 5
+    f = torch.from_numpy(gaussian_batch(N, range(2))).to(torch.complex64).cuda()
+    u = torch.empty_like(f)
+    prm = (ctypes.c_double * 4)(*ELL16)
+    st = torch.cuda.current_stream().cuda_stream
+    assert lib.fio_apply_noalloc(N, q, 1, prm, 4, 1, 3, 2, f.data_ptr(), u.data_ptr(), 2, st) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert lib.fio_apply_noalloc(N, q, 1, prm, 4, 1, 3, 2, f.data_ptr(), u.data_ptr(), 2, st) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
