@@ -387,7 +387,7 @@ def run_ours(args, rank, world, dist):
     prof = plan.profile_read()
     launches_per_step = plan.kernel_launches(NRHS)
     switch_impl = plan.info.switch_impl
-    trans_rs = plan.info.trans_rs
+    trans_rs = (plan.info.trans_rs, plan.info.trans_rs_x)
     sw_tile = plan.info.switch_rhs_tile
     u32 = u[0].cpu().numpy()
     # the adjoint apply (backward of the differentiable apply) on the same plan, outside the timed region
@@ -596,14 +596,21 @@ def run_small(args):
 
     n, r = args.small_n, args.small_nrhs
     plan = fio.Plan(n, Q, "ellipse", PARAMS, "f32", nrhs_max=r, s=S, e=E)
-    if args.switch_impl >= 0:
-        plan.set_switch(args.switch_impl)
+    if args.switch_impl >= 0 or args.trans_rs > 0 or args.trans_rs_x > 0:
+        plan.set_tuning(args.switch_impl, -1, args.trans_rs if args.trans_rs > 0 else -1,
+                        args.trans_rs_x if args.trans_rs_x > 0 else -1)
     f = torch.from_numpy(gaussian_batch(n, range(r))).to(torch.complex64).cuda()
     u = torch.empty_like(f)
     ms = time_steps(lambda: plan.apply(f, out=u), args.steps, args.warmup, torch)
     msa = time_steps(lambda: plan.adjoint(u, out=f), args.steps, args.warmup, torch)
+    plan.profile(True)
+    plan.apply(f, out=u)
+    plan.adjoint(u, out=f)
+    prof = plan.profile_read()
+    plan.profile(False)
     print(json.dumps({"case": "small", "N": n, "q": Q, "nrhs": r, "switch_impl": plan.info.switch_impl,
-                      "ms_forward": ms, "ms_adjoint": msa,
+                      "trans_rs": plan.info.trans_rs, "trans_rs_x": plan.info.trans_rs_x, "ms_forward": ms, "ms_adjoint": msa,
+                      "kernels_ms": {k: round(t / c, 3) for k, (c, t) in prof.items()},
                       "launches_per_apply": plan.kernel_launches(r)}), flush=True)
     plan.close()
 
@@ -620,7 +627,12 @@ def main():
     ap.add_argument("--small-n", type=int, default=256, help="--case small: N")
     ap.add_argument("--small-nrhs", type=int, default=16, help="--case small: right-hand sides")
     ap.add_argument("--switch-impl", type=int, default=-1,
-                    help="--case small: force the FP32 switch kernel (fio_plan_set_switch), -1 = autotuner")
+                    help="--case small: force the FP32 switch kernel (fio_plan_set_tuning), -1 = autotuner")
+    ap.add_argument("--trans-rs", type=int, default=0,
+                    help="--case small: force the FP32 translation kernel (2, 4, 8 RHS subtiles; 32, 33 "
+                         "register-tiled), 0 = autotuner")
+    ap.add_argument("--trans-rs-x", type=int, default=0,
+                    help="--case small: force the x-shape translation kernel (2, 4, 8; 32 register-tiled)")
     args = ap.parse_args()
     if args.case == "small":
         run_small(args)

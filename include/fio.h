@@ -147,10 +147,14 @@ typedef struct {
                               split TF32, kernel matrix in shared memory), 2 = FP32 FMA,
                               warp-specialised and persistent, 3 = tensor cores with the
                               kernel matrix in tensor memory (persistent, one CTA per SM) */
-  int trans_rs;            /* FIO_F32: right-hand sides per translation subtile (2, 4 or 8),
-                              chosen by fio_plan's autotuner */
+  int trans_rs;            /* FIO_F32, translations of the p-shape (recursion in p, eq. alg2b, and
+                              the adjoint of the recursion in x): right-hand sides per subtile
+                              (2, 4 or 8), or 32 for the register-tiled kernel (one RHS per lane,
+                              q <= 9); chosen by fio_plan's autotuner */
   int switch_rhs_tile;     /* FIO_F32, switch kernels 0 and 2: right-hand sides per contraction
                               task (4 or 8), chosen by fio_plan's autotuner */
+  int trans_rs_x;          /* FIO_F32, translations of the x-shape (recursion in x, eq. alg2c, and
+                              the adjoint of the recursion in p): 2, 4 or 8, or 32 (register-tiled) */
 } fio_plan_info_t;
 
 /* fio_plan_info -- copy the plan's parameters and sizes into *info. */
@@ -162,6 +166,15 @@ int fio_plan_info(fio_plan_t plan, fio_plan_info_t *info);
  * FIO_OK otherwise.  fio_apply_host calls it itself. */
 int fio_check(fio_plan_t plan, void *stream);
 
+/* fio_plan_set_wait_limit -- for tests of the failure path: the limit, in ns, of the
+ * waits by which the tensor-memory switch kernel (switch_impl 3) hands chunks between
+ * its producer warps and its MMA warp (0 restores the normal 2 s).  A tiny limit makes
+ * those waits expire: the kernel then records the expiry, stops issuing work, still waits
+ * with the normal limit for the tensor-core operations it issued, frees its tensor memory
+ * and returns; fio_check reports FIO_ETIMEOUT and the output of that apply is invalid.
+ * The paper has no counterpart. */
+int fio_plan_set_wait_limit(fio_plan_t plan, unsigned long long ns);
+
 /* fio_plan_set_switch -- override the autotuner's choice of the FIO_F32 switch
  * kernel: impl 0 = FP32 FMA, 1 = tensor cores (kernel matrix in shared memory),
  * 2 = warp-specialised FP32 FMA, 3 = tensor cores (kernel matrix in tensor memory).
@@ -171,9 +184,11 @@ int fio_plan_set_switch(fio_plan_t plan, int impl);
 
 /* fio_plan_set_tuning -- override every choice of fio_plan's autotuner for an FIO_F32
  * plan (a value of -1 keeps the current choice): switch_impl as fio_plan_set_switch,
- * switch_rhs_tile 4 or 8 (kernel 0 only; kernel 2 uses 4), trans_rs 2, 4 or 8.
+ * switch_rhs_tile 4 or 8 (kernel 0 only; kernel 2 uses 4); the translation kernels of
+ * each shape: trans_rs (p-shape) and trans_rs_x (x-shape), 2, 4 or 8 (RHS subtiles) or
+ * 32 (register-tiled kernels, q <= 9).
  * FIO_EINVAL for FIO_F64 plans or values outside those sets. */
-int fio_plan_set_tuning(fio_plan_t plan, int switch_impl, int switch_rhs_tile, int trans_rs);
+int fio_plan_set_tuning(fio_plan_t plan, int switch_impl, int switch_rhs_tile, int trans_rs, int trans_rs_x);
 
 /*
  * fio_apply_amplitude -- an FIO with a variable amplitude (eq. allfio),

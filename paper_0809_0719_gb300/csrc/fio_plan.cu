@@ -366,6 +366,7 @@ int fio_plan(fio_plan_t *out, int N, int q, int phase_id, const double *params, 
   // autotune the FP32 switch on this plan's shapes (kept for every later apply)
   d.switch_impl = 0;
   d.trans_rs = 8;
+  d.trans_rs_x = 8;
   d.sw_rb = 4;
   if (precision == FIO_F32) {
     int impl = 0;
@@ -484,6 +485,7 @@ int fio_plan_info(fio_plan_t p, fio_plan_info_t *info) {
   info->max_box_sources = d.maxsrc;
   info->switch_impl = d.switch_impl;
   info->trans_rs = d.trans_rs;
+  info->trans_rs_x = d.trans_rs_x;
   info->switch_rhs_tile = d.sw_rb;
   return FIO_OK;
 }
@@ -571,19 +573,30 @@ int fio_plan_set_switch(fio_plan_t p, int impl) {
   return FIO_OK;
 }
 
-int fio_plan_set_tuning(fio_plan_t p, int switch_impl, int switch_rhs_tile, int trans_rs) {
+int fio_plan_set_wait_limit(fio_plan_t p, unsigned long long ns) {
+  if (!p) return fail(FIO_EINVAL, "plan is NULL");
+  p->d.handoff_ns = ns;
+  return FIO_OK;
+}
+
+int fio_plan_set_tuning(fio_plan_t p, int switch_impl, int switch_rhs_tile, int trans_rs, int trans_rs_x) {
   if (!p) return fail(FIO_EINVAL, "plan is NULL");
   if (p->d.precision != FIO_F32) return fail(FIO_EINVAL, "only FIO_F32 plans are tuned");
   if (switch_rhs_tile != -1 && switch_rhs_tile != 4 && switch_rhs_tile != 8)
     return fail(FIO_EINVAL, "switch_rhs_tile %d must be 4 or 8", switch_rhs_tile);
-  if (trans_rs != -1 && trans_rs != 2 && trans_rs != 4 && trans_rs != 8)
-    return fail(FIO_EINVAL, "trans_rs %d must be 2, 4 or 8", trans_rs);
+  if (trans_rs != -1 && trans_rs != 2 && trans_rs != 4 && trans_rs != 8 && trans_rs != 32)
+    return fail(FIO_EINVAL, "trans_rs %d must be 2, 4, 8 or 32", trans_rs);
+  if (trans_rs_x != -1 && trans_rs_x != 2 && trans_rs_x != 4 && trans_rs_x != 8 && trans_rs_x != 32)
+    return fail(FIO_EINVAL, "trans_rs_x %d must be 2, 4, 8 or 32", trans_rs_x);
+  if ((trans_rs >= 32 || trans_rs_x >= 32) && p->d.q > 9)
+    return fail(FIO_EINVAL, "the register-tiled translations (trans_rs 32) are compiled for q <= 9");
   if (switch_impl != -1) {
     const int rc = fio_plan_set_switch(p, switch_impl);
     if (rc) return rc;
   }
   if (switch_rhs_tile != -1) p->d.sw_rb = switch_rhs_tile;
   if (trans_rs != -1) p->d.trans_rs = trans_rs;
+  if (trans_rs_x != -1) p->d.trans_rs_x = trans_rs_x;
   return FIO_OK;
 }
 

@@ -3,7 +3,7 @@
 #pragma once
 #include <algorithm>
 
-#include "fio_tc.cuh"
+#include "fio_k32r.cuh"
 
 namespace fio {
 
@@ -39,9 +39,14 @@ struct PlanDev {
   int num_sms;
   int switch_impl;  // FP32 switch: 0 FFMA, 1 tensor cores (A in smem), 2 warp-specialised FFMA,
                     // 3 tensor cores (A in tensor memory); chosen by the plan's autotuner
-  int trans_rs;     // FP32 translations: RHS per subtile, 2, 4 or 8 (chosen by the plan's autotuner)
+  int trans_rs;     // FP32 translations of the p-shape (recursion in p, adjoint of the recursion
+                    // in x): RHS per subtile 2, 4 or 8, or 32 for the register-tiled kernels
+                    // (fio_k32r.cuh, q <= 9); chosen by the plan's autotuner
+  int trans_rs_x;   // the same for the x-shape (recursion in x, adjoint of the recursion in p):
+                    // 2, 4, 8, or 32 (register-tiled)
   int sw_rb;        // FP32 FFMA switch: RHS per contraction task, 4 or 8 (chosen by the plan's autotuner)
   int *status;  // device status word: 1 = a bounded wait expired (read by fio_check)
+  unsigned long long handoff_ns;  // tensor-memory switch: limit of its hand-off waits (0 = normal; tests)
   Prof *prof;   // NULL unless profiling was ever enabled
 };
 
@@ -124,12 +129,42 @@ template <typename R, int Q> struct Runner {
     return check();
   }
 
+  // Register-tiled translation (32 RHS per CTA, one per lane).
+  template <bool TYPE_P, bool FWD> int trans32r(int l, const CT *in, CT *out) {
+    if constexpr (Q <= 9) {
+      const long long nunits = (1LL << (2 * (l - 1))) * nb_at(p.L - l);
+      const Geom g = geom(l, kRT, 1, nunits);
+      dim3 grid((unsigned)nunits, (unsigned)((nrhs + kRT - 1) / kRT));
+      if (count_only) return check();
+      pre(TYPE_P ? (FWD ? K_TRANS_P : K_TRANS_P_ADJ) : (FWD ? K_TRANS_X : K_TRANS_X_ADJ));
+      if (TYPE_P) {
+        auto k = k32_trans_rp<Q, FWD>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, 4 * kRT, trans_rp_smem_bytes(Q), st>>>(p.tb, p.tf, p.ph, g, tmat(), (const float2 *)in, (float2 *)out,
+                                                        p.status);
+      } else {
+        auto k = k32_trans_rx<Q, FWD>;
+        set_smem(k, p.smem_optin);
+        k<<<grid, 4 * kRT, trans_rx_smem_bytes(Q), st>>>(p.tb, p.tf, p.ph, g, tmat(), (const float2 *)in, (float2 *)out,
+                                                        p.status);
+      }
+      return check();
+    }
+    return (int)cudaErrorInvalidConfiguration;
+  }
+  bool trans_r_ok() const {
+    return fast32() && Q <= 9 && p.status && trans_rp_smem_bytes(Q) <= p.smem_optin &&
+           trans_rx_smem_bytes(Q) <= p.smem_optin;
+  }
+
   // Translation at level l (forward: l-1 -> l; adjoint: l -> l-1).
   template <bool TYPE_P, bool FWD> int trans(int l, const CT *in, CT *out) {
     if constexpr (sizeof(R) == 4) {
       if (fast32()) {
-        if (p.trans_rs == 2) return trans32<TYPE_P, FWD, 2>(l, in, out);
-        if (p.trans_rs == 4) return trans32<TYPE_P, FWD, 4>(l, in, out);
+        const int rs = TYPE_P ? p.trans_rs : p.trans_rs_x;
+        if (rs == 32 && trans_r_ok()) return trans32r<TYPE_P, FWD>(l, in, out);
+        if (rs == 2) return trans32<TYPE_P, FWD, 2>(l, in, out);
+        if (rs == 4) return trans32<TYPE_P, FWD, 4>(l, in, out);
         return trans32<TYPE_P, FWD, 8>(l, in, out);
       }
     }
@@ -179,7 +214,8 @@ template <typename R, int Q> struct Runner {
         pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
         auto k = k32_switch_tm<Q, FWD>;
         set_smem(k, p.smem_optin);
-        k<<<grid, kTmThreads, smem_tm, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, p.status);
+        k<<<grid, kTmThreads, smem_tm, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, p.status,
+                                             p.handoff_ns);
         return check();
       }
       const size_t smem_tc = TcShape<Q>::smem_bytes();
@@ -402,20 +438,31 @@ template <typename R, int Q> struct Runner {
       if (!fast32()) return 0;
       const CT *s0 = (const CT *)p.state[0];
       CT *s1 = (CT *)p.state[1];
-      if (p.l1 > p.l0) {  // translation subtile width
-        const int l = p.lm > p.l0 ? p.l0 + 1 : p.lm + 1;
-        const bool tp = p.lm > p.l0;
-        float best = 1e30f;
-        int pick = 8;
-        for (int rs : {2, 4, 8}) {
-          pm.trans_rs = rs;
-          const float ms = best_ms([&]() { tp ? trans<true, true>(l, s0, s1) : trans<false, true>(l, s0, s1); });
-          if (ms < best) {
-            best = ms;
-            pick = rs;
+      if (p.l1 > p.l0) {  // translation kernels: RHS subtile width or the register-tiled kernels,
+        // for each shape on its own (timed on a forward level of that shape if the plan has
+        // one, else on the adjoint level that uses it)
+        const bool has_p = p.lm > p.l0, has_x = p.l1 > p.lm;
+        for (int shape = 0; shape < 2; shape++) {
+          float best = 1e30f;
+          int pick = 8;
+          for (int rs : {2, 4, 8, 32}) {
+            if (rs == 32 && !trans_r_ok()) continue;
+            int &field = shape == 0 ? pm.trans_rs : pm.trans_rs_x;
+            field = rs;
+            float ms;
+            if (shape == 0)
+              ms = has_p ? best_ms([&]() { trans<true, true>(p.l0 + 1, s0, s1); })
+                         : best_ms([&]() { trans<true, false>(p.lm + 1, s0, s1); });
+            else
+              ms = has_x ? best_ms([&]() { trans<false, true>(p.lm + 1, s0, s1); })
+                         : best_ms([&]() { trans<false, false>(p.l0 + 1, s0, s1); });
+            if (ms < best) {
+              best = ms;
+              pick = rs;
+            }
           }
+          (shape == 0 ? pm.trans_rs : pm.trans_rs_x) = pick;
         }
-        pm.trans_rs = pick;
       }
       const int avail = switch_impls();
       float best = 1e30f;

@@ -88,9 +88,23 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity) {
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity, unsigned long long limit_ns = kTcWaitNs) {
   const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
   const unsigned long long t0 = globaltimer_ns();
+  if (limit_ns < kTcSuspendNs) {
+    // short limits (tests of the failure path): non-blocking polls, so the limit is exact
+    for (uint32_t it = 1; it < (1u << 26); it++) {
+      uint32_t done;
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(mb), "r"(parity)
+          : "memory");
+      if (done) return true;
+      if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+  }
   for (uint32_t it = 1; it < (1u << 26); it++) {  // the wall-time bound normally ends it first
     uint32_t done;
     asm volatile(
@@ -99,7 +113,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity) {
         : "r"(mb), "r"(parity), "r"(kTcSuspendNs)
         : "memory");
     if (done) return true;
-    if (globaltimer_ns() - t0 > kTcWaitNs) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -465,10 +479,14 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float *v) {
 }
 __device__ __forceinline__ void tm_arrive(uint64_t *mbar) { mbar_arrive(mbar); }
 
+// handoff_ns: limit of the waits between the producer warps and the MMA warp (0: the
+// normal 2 s); a test sets it tiny to make them expire.  The final drain of the issued
+// MMAs (fin) always waits with the normal limit.
 template <int Q, bool FWD>
 __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, TablesF tf, Phase ph, Geom g,
                                                                 const float2 *__restrict__ in,
-                                                                float2 *__restrict__ out, int *status) {
+                                                                float2 *__restrict__ out, int *status,
+                                                                unsigned long long handoff_ns) {
   typedef TmShape<Q> S;
   constexpr int Q2 = S::Q2, KS = S::KS, NCH = S::NCH;
   constexpr int CPW = kTmKC / 2 / kTmPQ;  // complex kernel columns per producer warp and chunk
@@ -526,8 +544,9 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_s;
   // bounded wait with a warp-uniform outcome; on expiry record the status and raise the abort flag
+  const unsigned long long hlim = handoff_ns ? handoff_ns : kTcWaitNs;
   auto waitw = [&](uint64_t *mb, uint32_t parity) {
-    bool ok = !*abort_s && tc_wait(mb, parity);
+    bool ok = !*abort_s && tc_wait(mb, parity, hlim);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok && lane == 0) {
       atomicExch(status, 1);

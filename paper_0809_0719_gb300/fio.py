@@ -44,7 +44,7 @@ class PlanInfo(ctypes.Structure):
                                             "nrhs_max", "nstages")] + [
         ("pairs_per_level", ctypes.c_longlong), ("state_bytes", ctypes.c_longlong),
         ("table_bytes", ctypes.c_longlong), ("max_box_sources", ctypes.c_int), ("switch_impl", ctypes.c_int),
-        ("trans_rs", ctypes.c_int), ("switch_rhs_tile", ctypes.c_int)]
+        ("trans_rs", ctypes.c_int), ("switch_rhs_tile", ctypes.c_int), ("trans_rs_x", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -74,7 +74,8 @@ def lib() -> ctypes.CDLL:
             L.fio_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ip, ctypes.POINTER(ip)]
             L.fio_peak_probe.argtypes = [ip, ctypes.POINTER(ctypes.c_double)]
             L.fio_plan_set_switch.argtypes = [vp, ip]
-            L.fio_plan_set_tuning.argtypes = [vp, ip, ip, ip]
+            L.fio_plan_set_wait_limit.argtypes = [vp, ctypes.c_ulonglong]
+            L.fio_plan_set_tuning.argtypes = [vp, ip, ip, ip, ip]
             L.fio_direct.argtypes = [vp, vp, ip, vp, ip, vp, vp]
             L.fio_apply_amplitude.argtypes = [vp, vp, vp, vp, ip, vp, ip, ip, vp]
             L.fio_apply_wave.argtypes = [vp, vp, vp, vp, ip, ctypes.c_double, ctypes.c_double, ip, vp]
@@ -215,10 +216,16 @@ class Plan:
         _check(lib().fio_plan_set_switch(self._h, int(impl)))
         self.info.switch_impl = int(impl)
 
-    def set_tuning(self, switch_impl: int = -1, switch_rhs_tile: int = -1, trans_rs: int = -1) -> None:
+    def set_tuning(self, switch_impl: int = -1, switch_rhs_tile: int = -1, trans_rs: int = -1,
+                   trans_rs_x: int = -1) -> None:
         """fio_plan_set_tuning: override the autotuner's choices (-1 keeps one)."""
-        _check(lib().fio_plan_set_tuning(self._h, int(switch_impl), int(switch_rhs_tile), int(trans_rs)))
+        _check(lib().fio_plan_set_tuning(self._h, int(switch_impl), int(switch_rhs_tile), int(trans_rs),
+                                         int(trans_rs_x)))
         _check(lib().fio_plan_info(self._h, ctypes.byref(self.info)))
+
+    def set_wait_limit(self, ns: int) -> None:
+        """fio_plan_set_wait_limit: limit of the tensor-memory switch's hand-off waits (0 = normal)."""
+        _check(lib().fio_plan_set_wait_limit(self._h, int(ns)))
 
     def check(self, stream=None) -> None:
         """fio_check: synchronise and raise if a bounded device-side wait expired."""

@@ -77,7 +77,7 @@ def test_calls_on_null_plan_fail_cleanly(lib):
     assert lib.fio_destroy(None) == 0
     for impl in (0, 1, 2, 3):  # every switch kernel id, including the tensor-memory one
         assert lib.fio_plan_set_switch(None, impl) == -1
-    assert lib.fio_plan_set_tuning(None, 3, -1, -1) == -1
+    assert lib.fio_plan_set_tuning(None, 3, -1, -1, -1) == -1
     assert lib.fio_apply_wave(None, None, None, None, 1, ctypes.c_double(0.5), ctypes.c_double(0.5), 0, None) == -1
 
 
@@ -114,7 +114,7 @@ def test_auto_and_direct_reject_bad_arguments_without_a_gpu(lib):
     assert lib.fio_plan_auto(ctypes.byref(h), 64, 1, prm, 4, 1, 1, -1, -1, 0.0, 16, 0, None, None) == -1   # target
     assert lib.fio_plan_auto(ctypes.byref(h), 64, 1, prm, 4, 1, 1, -1, -1, 1e-3, 0, 0, None, None) == -1   # nsample
     assert lib.fio_direct(None, None, 1, None, 1, None, None) == -1
-    assert lib.fio_plan_set_tuning(None, -1, -1, -1) == -1
+    assert lib.fio_plan_set_tuning(None, -1, -1, -1, -1) == -1
 
 
 def test_amplitude_rejects_bad_arguments_without_a_gpu(lib):

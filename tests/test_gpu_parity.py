@@ -174,8 +174,9 @@ def test_every_tuning_choice_matches_oracle(fio, oracle, N, q, phase, nrhs, sw, 
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, "f32", nrhs_max=nrhs)
     try:
-        plan.set_tuning(sw, tile, rs)
-        assert (plan.info.switch_impl, plan.info.switch_rhs_tile, plan.info.trans_rs) == (sw, tile, rs)
+        plan.set_tuning(sw, tile, rs, rs)
+        assert (plan.info.switch_impl, plan.info.switch_rhs_tile, plan.info.trans_rs, plan.info.trans_rs_x) == (
+            sw, tile, rs, rs)
         F = gaussian_batch(N, range(300, 300 + nrhs))
         U = plan.apply(torch.from_numpy(F).to(plan.dtype).cuda()).cpu().numpy()
         G = plan.adjoint(torch.from_numpy(F).to(plan.dtype).cuda()).cpu().numpy()
@@ -301,5 +302,36 @@ def test_tensor_memory_switch_matches_fma_switch(fio, N, q, nrhs):
             a, b = out[3][k], out[0][k]
             for r in range(nrhs):
                 assert rel(a[r].cpu().numpy(), b[r].cpu().numpy()) < 2e-6, (k, r)
+    finally:
+        plan.close()
+
+
+# register-tiled translations (trans_rs 32 for the p-shape, trans_rs_x 32 for the x-shape),
+# each shape also beside the other's subtile kernel.  Cases cover the
+# bulk-copy staging (even RHS counts), the cp.async fallback (odd counts), full and
+# partial 32-RHS tiles, several tiles, s = 0 (three levels of each recursion) and
+# every phase
+REG_CASES = [(64, 9, "ellipse", 32, 3, 2), (128, 7, "circle", 10, 3, 2), (64, 5, "ellipse", 33, 0, 2),
+             (32, 3, "separable", 2, 0, 1), (128, 9, "linear", 64, 3, 0)]
+
+
+@pytest.mark.parametrize("N,q,phase,nrhs,s,e", REG_CASES)
+@pytest.mark.parametrize("rs,rsx", [(32, 32), (32, 4), (8, 32)])
+def test_register_tiled_translations_match_oracle(fio, oracle, N, q, phase, nrhs, s, e, rs, rsx):
+    pid, prm = PH[phase]
+    plan = fio.Plan(N, q, pid, prm, "f32", nrhs_max=nrhs, s=s, e=e)
+    try:
+        plan.set_tuning(-1, -1, rs, rsx)
+        assert (plan.info.trans_rs, plan.info.trans_rs_x) == (rs, rsx)
+        F = gaussian_batch(N, range(500, 500 + nrhs))
+        f = torch.from_numpy(F).to(plan.dtype).cuda()
+        U = plan.apply(f).cpu().numpy()
+        G = plan.adjoint(f).cpu().numpy()
+        plan.check()  # no bounded wait on the staging expired
+        for r in sorted({0, nrhs // 2, nrhs - 1}):
+            Fr = F[r].astype(np.complex64).astype(np.complex128)
+            assert rel(U[r], oracle_bf(oracle, N, q, phase, Fr, plan.info.s, e)) < F32_TOL, r
+            ref = oracle.butterfly_adjoint(N, q, pid, list(prm), Fr, s=plan.info.s, e=e)
+            assert rel(G[r], ref) < F32_TOL, r
     finally:
         plan.close()
