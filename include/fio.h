@@ -227,6 +227,26 @@ int fio_apply_wave(fio_plan_t plus, fio_plan_t minus, const void *in, void *out,
                    double w_minus, int adjoint, void *stream);
 
 /*
+ * fio_apply_wave_series -- the wave propagator at several times from ONE plan (Sec. 1):
+ *     out[k] = 1/2 (B_{+t_k} in + B_{-t_k} in),   k = 0 .. ntimes-1,
+ * where B_{+-t} has the phase lambda x.k +- t c(x)|k|, c(x) = (a + m sin 2 pi x1 sin 2 pi x2)/b,
+ * and plan is a FIO_PHASE_CIRCLE plan with params [a, m, b, lambda] (the speed at t = 1).
+ * With lambda = 1 and in the Fourier coefficients of u(x, 0), out[k] is u(x, t_k) for
+ * u_tt = c^2 Lap u, u_t(x, 0) = 0 (exactly for constant c).  Every one of the 2 ntimes
+ * butterflies runs on this plan's node, source and Lagrange tables and its two state
+ * buffers -- the tables do not depend on the phase, only the kernels' phase arguments
+ * change -- so the series needs one plan's device memory (fio_plan_info().table_bytes +
+ * state_bytes, plus one staging buffer of nrhs_max N^2 elements allocated on first use)
+ * instead of 2 ntimes plans'.  Each out[k] is bit-identical to fio_apply_wave on a
+ * separately built pair of plans with params [+-a t_k, +-m t_k, b, lambda].
+ *   times  HOST, ntimes values
+ *   in     DEVICE (nrhs, N, N); out DEVICE (ntimes, nrhs, N, N); not overlapping
+ * Enqueued on `stream`; uses the plan's state: one call at a time per plan.
+ */
+int fio_apply_wave_series(fio_plan_t plan, const double *times, int ntimes, const void *in, void *out, int nrhs,
+                          void *stream);
+
+/*
  * fio_direct -- the operator itself (eq. dfio), summed directly on the GPU at sampled
  * grid points: out[r][i] = sum_k e^{2 pi i Phi(x_i,k)} f[r](k), x_i = the flat grid index
  * xi[i] = i1 * N + i2.  Every term of the N^2 is evaluated (O(N^2) per point), the phase as

@@ -39,6 +39,33 @@ __global__ void k_wave_sum(CT *__restrict__ y, const CT *__restrict__ v, R wp, R
   }
 }
 
+int run_any(const PlanDev &d, int kind, const void *in, void *out, int nrhs, cudaStream_t st) {
+  switch (d.q) {
+  case 3: return run_q3(d, kind, in, out, nrhs, st, -1, nullptr);
+  case 5: return run_q5(d, kind, in, out, nrhs, st, -1, nullptr);
+  case 7: return run_q7(d, kind, in, out, nrhs, st, -1, nullptr);
+  case 9: return run_q9(d, kind, in, out, nrhs, st, -1, nullptr);
+  case 11: return run_q11(d, kind, in, out, nrhs, st, -1, nullptr);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+// The c(x)|k| phase lambda x.k + s t (a + m sin 2 pi x1 sin 2 pi x2)|k| / b (s = +-1) on a
+// copy of the plan's device description: the node, source and Lagrange tables do not
+// depend on the phase, only the kernels' Phase arguments do.
+void set_wave_phase(PlanDev &d, const Phase &base, double sign_t) {
+  d.ph = base;
+  d.ph.a = base.a * sign_t;
+  d.ph.m = base.m * sign_t;
+  if (d.precision == FIO_F32) {
+    d.tf.ph.id = d.ph.id;
+    d.tf.ph.a = df_split(d.ph.a);
+    d.tf.ph.m = df_split(d.ph.m);
+    d.tf.ph.ib = df_split(d.ph.ib);
+    d.tf.ph.lam = df_split(d.ph.lam);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -83,3 +110,49 @@ int fio_apply_wave(fio_plan_t plus, fio_plan_t minus, const void *in, void *out,
 }
 
 }  // extern "C"
+
+extern "C" int fio_apply_wave_series(fio_plan_t plan, const double *times, int ntimes, const void *in, void *out,
+                                     int nrhs, void *stream) {
+  if (!plan) return wfail(FIO_EINVAL, "plan is NULL");
+  if (plan->d.ph.id != FIO_PHASE_CIRCLE) return wfail(FIO_EINVAL, "fio_apply_wave_series needs a FIO_PHASE_CIRCLE plan");
+  if (!times || ntimes < 1) return wfail(FIO_EINVAL, "need ntimes >= 1 times");
+  if (!in || !out) return wfail(FIO_EINVAL, "NULL data pointer");
+  if (((uintptr_t)in | (uintptr_t)out) & 15) return wfail(FIO_EINVAL, "data pointers must be 16-byte aligned");
+  if (nrhs < 1 || nrhs > plan->d.nrhs_max) return wfail(FIO_EINVAL, "nrhs=%d must be in [1, %d]", nrhs, plan->d.nrhs_max);
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != plan->device) return wfail(FIO_EINVAL, "plan was built on device %d but device %d is current", plan->device, dev);
+  const bool f64 = plan->d.precision == FIO_F64;
+  const size_t eb = f64 ? 16 : 8;
+  const long long n = (long long)nrhs * plan->d.N * plan->d.N;
+  if ((const char *)in < (const char *)out + (size_t)ntimes * n * eb && (const char *)out < (const char *)in + n * eb)
+    return wfail(FIO_EINVAL, "in and out overlap");
+  if (!plan->stage_buf[0]) {  // the plan's staging buffers (nrhs_max N^2 elements each)
+    const size_t bytes = (size_t)plan->d.N * plan->d.N * eb * plan->d.nrhs_max;
+    for (int i = 0; i < 2; i++) {
+      const cudaError_t ce = cudaMalloc(&plan->stage_buf[i], bytes);
+      if (ce != cudaSuccess) return wfail(FIO_ENOMEM, "cudaMalloc(staging): %s", cudaGetErrorString(ce));
+    }
+    plan->stage_bytes = bytes;
+  }
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int grid = 4 * std::max(1, plan->d.num_sms), block = 256;
+  PlanDev d = plan->d;  // phases change per launch; tables and state buffers are the plan's
+  void *tmp = plan->stage_buf[0];
+  for (int k = 0; k < ntimes; k++) {
+    char *uk = (char *)out + (size_t)k * n * eb;
+    set_wave_phase(d, plan->d.ph, times[k]);
+    int rc = run_any(d, RUN_FWD, in, uk, nrhs, st);
+    if (rc) return wfail(FIO_ECUDA, "wave series, B+ at t=%g: %s", times[k], cudaGetErrorString((cudaError_t)rc));
+    set_wave_phase(d, plan->d.ph, -times[k]);
+    rc = run_any(d, RUN_FWD, in, tmp, nrhs, st);
+    if (rc) return wfail(FIO_ECUDA, "wave series, B- at t=%g: %s", times[k], cudaGetErrorString((cudaError_t)rc));
+    if (f64)
+      k_wave_sum<double2, double><<<grid, block, 0, st>>>((double2 *)uk, (const double2 *)tmp, 0.5, 0.5, n);
+    else
+      k_wave_sum<float2, float><<<grid, block, 0, st>>>((float2 *)uk, (const float2 *)tmp, 0.5f, 0.5f, n);
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return wfail(FIO_ECUDA, "wave sum: %s", cudaGetErrorString(ce));
+  }
+  return FIO_OK;
+}

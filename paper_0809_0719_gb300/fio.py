@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             L.fio_direct.argtypes = [vp, vp, ip, vp, ip, vp, vp]
             L.fio_apply_amplitude.argtypes = [vp, vp, vp, vp, ip, vp, ip, ip, vp]
             L.fio_apply_wave.argtypes = [vp, vp, vp, vp, ip, ctypes.c_double, ctypes.c_double, ip, vp]
+            L.fio_apply_wave_series.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ip, vp, vp, ip, vp]
             L.fio_plan_auto.argtypes = [ctypes.POINTER(vp), ip, ip, ctypes.POINTER(ctypes.c_double), ip, ip, ip, ip,
                                         ip, ctypes.c_double, ip, ctypes.c_ulonglong, ctypes.POINTER(ip),
                                         ctypes.POINTER(ctypes.c_double)]
@@ -380,6 +381,21 @@ def apply_wave(plus: Plan, minus: Plan, x: torch.Tensor, w_plus: float = 0.5, w_
     out = torch.empty_like(x) if out is None else plus._dev_tensor(out, "out")
     _check(lib().fio_apply_wave(plus._h, minus._h, x.data_ptr(), out.data_ptr(), x.shape[0], float(w_plus),
                                 float(w_minus), int(adjoint), _stream_ptr(stream)))
+    return out
+
+
+def apply_wave_series(plan: Plan, times, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """fio_apply_wave_series: u(t_k) = (B_{+t_k} x + B_{-t_k} x)/2 for every t_k from one circle-phase
+    plan (its params give the speed at t = 1); returns (ntimes, nrhs, N, N)."""
+    x = plan._dev_tensor(x, "input")
+    times = [float(t) for t in times]
+    shape = (len(times),) + tuple(x.shape)
+    out = torch.empty(shape, dtype=x.dtype, device=x.device) if out is None else out
+    if tuple(out.shape) != shape or out.dtype != x.dtype or not out.is_contiguous():
+        raise ValueError("out must be a contiguous %s tensor of shape %s" % (x.dtype, shape))
+    ts = (ctypes.c_double * len(times))(*times)
+    _check(lib().fio_apply_wave_series(plan._h, ts, len(times), x.data_ptr(), out.data_ptr(), x.shape[0],
+                                       _stream_ptr(stream)))
     return out
 
 

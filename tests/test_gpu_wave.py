@@ -84,3 +84,39 @@ def test_wave_rejects_mismatched_plans(fio):
     finally:
         p32.close()
         p64.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_wave_series_from_one_plan(fio, oracle, prec, tol):
+    # u(t_k) for several times from ONE circle-phase plan (its tables and state serve all 2 ntimes
+    # butterflies): against the oracle's two-phase butterfly at each time, and bit for bit
+    # against fio_apply_wave on a separately built pair of plans per time
+    N, q, R = 64, 7, 2
+    times = [0.3, 1.0, 2.5]
+    plan = fio.Plan(N, q, "circle", (A, M, B, 1.0), prec, nrhs_max=R, e=2)
+    try:
+        F = gaussian_batch(N, range(600, 600 + R))
+        f = torch.from_numpy(F).to(plan.dtype).cuda()
+        U = fio.apply_wave_series(plan, times, f)
+        plan.check()
+        Uh = U.cpu().numpy()
+        for k, t in enumerate(times):
+            plus, minus = fio.wave_plans(N, q, A, M, B, t, prec, nrhs_max=R, e=2)
+            try:
+                pair = fio.apply_wave(plus, minus, f)
+                assert torch.equal(pair, U[k]), (k, t)
+            finally:
+                plus.close()
+                minus.close()
+            for r in range(R):
+                fr = F[r].astype(np.complex64).astype(np.complex128) if prec == "f32" else F[r]
+                ref = oracle.wave_butterfly(N, q, A, M, B, t, fr, s=plan.info.s, e=2)
+                assert rel(Uh[k, r], ref) < tol, (k, r, rel(Uh[k, r], ref))
+        with pytest.raises(fio.FIOError):  # a linear-phase plan has no speed to propagate with
+            lin = fio.Plan(N, q, "linear", (), prec)
+            try:
+                fio.apply_wave_series(lin, times, f[:1])
+            finally:
+                lin.close()
+    finally:
+        plan.close()
