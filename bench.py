@@ -444,6 +444,9 @@ def run_ours(args, rank, world, dist):
     # ---- the wave propagator as a sum of two FIOs (every rank: replicas)
     wave = run_wave(args, dev, tmax, world)
 
+    # ---- the three-dimensional butterfly (every rank: replicas)
+    b3 = run_3d(args, dev, tmax, world, with_errors=rank == 0)
+
     # ---- the uneven batch of plans (every rank: replicas)
     ub = run_uneven_batch(args, dev, with_errors=rank == 0) if args.batch else None
 
@@ -482,6 +485,7 @@ def run_ours(args, rank, world, dist):
         "peak_probes": probes,
         "uneven_batch": ub,
         "wave": wave,
+        "butterfly_3d": b3,
         "amplitude": {"value": whole_job_rate(N * N * na, ms_amp, world), "unit": "outputs/s", "ms_per_step": ms_amp,
                       "what": "fio_apply_amplitude: %d inputs x %d separated amplitude terms (eq. allfio) as one "
                               "32-RHS butterfly" % (na, nt)},
@@ -533,6 +537,52 @@ def run_wave(args, dev, tmax, world):
                 "value": whole_job_rate(n * n * NRHS * len(WAVE_TIMES), ms, world), "unit": "outputs/s",
                 "ms_per_step": ms, "api": "fio_apply_wave_series (one plan's tables and state for all phases)",
                 "device_bytes": one, "device_bytes_one_plan_per_phase": 2 * len(WAVE_TIMES) * (one - n * n * NRHS * 8)}
+    except Exception as ex:  # reported, not raised
+        return {"error": "%s: %s" % (type(ex).__name__, ex)}
+    finally:
+        if plan is not None:
+            plan.close()
+        torch.cuda.empty_cache()
+
+
+N3, Q3, E3 = 64, 7, 1
+EX3 = (3.0, 1.0, 4.0, 1.0)
+
+
+def run_3d(args, dev, tmax, world, with_errors=True):
+    """The three-dimensional butterfly (fio3_apply, FP64) on Table 3's workload: N = 64, q = 7,
+    the phase of eq. ex3 (c(x) = (3 + sin sin sin)/4), white-noise sources, one RHS, e = 1,
+    s = 3.  Outputs/s = N^3 / time; the error is eq. err on 64 seeded x against the oracle's
+    3D direct sum (the reference values of the CPU-baseline leg).  A failure is reported in
+    the result instead of raised."""
+    import torch
+
+    from paper_0809_0719_gb300 import fio
+
+    plan = None
+    try:
+        plan = fio.Plan3(N3, Q3, "sphere", EX3, nrhs_max=1, s=3, e=E3)
+        rng = np.random.default_rng(0)
+        F = rng.standard_normal((N3, N3, N3)) + 1j * rng.standard_normal((N3, N3, N3))
+        f = torch.from_numpy(F[None]).to(dev)
+        u = torch.empty_like(f)
+        ms = tmax(time_steps(lambda: plan.apply(f, out=u), 1, 1, torch))
+        rec = {"workload": "3D butterfly N=%d q=%d eq. ex3, e=%d s=3, 1 RHS, FP64 form (Table 3)" % (N3, Q3, E3),
+               "value": whole_job_rate(N3 ** 3, ms, world), "unit": "outputs/s", "ms_per_step": ms,
+               "api": "fio3_apply", "paper_table3_eps_a": 3.32e-3}
+        if with_errors:
+            from oracle import oracle as O
+
+            xi = np.sort(np.random.default_rng(1000).choice(N3 ** 3, 64, replace=False)).astype(np.int64)
+            t0 = time.perf_counter()
+            ref = O.direct3(N3, O.SPHERE, list(EX3), F, xi)
+            dt = time.perf_counter() - t0
+            a = u.cpu().numpy().reshape(-1)[xi]
+            rec["rel_l2_err"] = float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+            rec["cpu_direct_sum"] = {"value": 64 / dt, "unit": "outputs/s", "cores": O.threads(),
+                                     "sample": "FP64 3D direct sum at 64 seeded x"}
+        del f, u
+        return rec
     except Exception as ex:  # reported, not raised
         return {"error": "%s: %s" % (type(ex).__name__, ex)}
     finally:

@@ -47,6 +47,12 @@ class PlanInfo(ctypes.Structure):
         ("trans_rs", ctypes.c_int), ("switch_rhs_tile", ctypes.c_int), ("trans_rs_x", ctypes.c_int)]
 
 
+class PlanInfo3(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("N", "L", "q", "s", "e", "l0", "lm", "l1", "phase_id", "nrhs_max")] + [
+        ("pairs_per_level", ctypes.c_longlong), ("state_bytes", ctypes.c_longlong),
+        ("table_bytes", ctypes.c_longlong), ("max_box_sources", ctypes.c_int)]
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("nplans", "ngroups", "launches_fwd", "launches_adj", "parallel_groups",
                                             "tuned")] + [("total_elems", ctypes.c_longlong), ("tune_ms", ctypes.c_double)]
@@ -95,6 +101,11 @@ def lib() -> ctypes.CDLL:
             L.fio_apply_batch_adjoint.argtypes = L.fio_apply_batch.argtypes
             L.fio_workspace_bytes.argtypes = [vp, ip]
             L.fio_workspace_bytes.restype = ctypes.c_size_t
+            L.fio3_plan.argtypes = [ctypes.POINTER(vp), ip, ip, ip, ctypes.POINTER(ctypes.c_double), ip, ip, ip, ip]
+            L.fio3_destroy.argtypes = [vp]
+            L.fio3_apply.argtypes = [vp, vp, vp, ip, vp]
+            L.fio3_apply_adjoint.argtypes = [vp, vp, vp, ip, vp]
+            L.fio3_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo3)]
             L.fio_last_error.restype = ctypes.c_char_p
             _lib = L
         return _lib
@@ -249,6 +260,63 @@ class Plan:
         n = ctypes.c_int()
         _check(lib().fio_profile_read(self._h, buf, 16, ctypes.byref(n)))
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms)) for i in range(n.value)}
+
+
+class Plan3:
+    """The three-dimensional butterfly (include/fio3.h), FP64: fio3_plan(N, q, phase, params,
+    nrhs_max, s, e).  Tensors are (nrhs, N, N, N) complex128; f[r, k1+N/2, k2+N/2, k3+N/2] is the
+    source at k, u[r, i1, i2, i3] the potential at x = (i1, i2, i3)/N."""
+
+    PHASES3 = {"linear": 0, "sphere": 2}
+
+    def __init__(self, N: int, q: int, phase="sphere", params=(3.0, 1.0, 4.0, 1.0), nrhs_max: int = 1, s: int = -1,
+                 e: int = -1):
+        self._h = None
+        L = lib()
+        pid = self.PHASES3[phase] if isinstance(phase, str) else int(phase)
+        prm = [] if pid == 0 else list(params)
+        arr = (ctypes.c_double * max(1, len(prm)))(*prm)
+        h = ctypes.c_void_p()
+        _check(L.fio3_plan(ctypes.byref(h), N, q, pid, arr, len(prm), nrhs_max, s, e))
+        self._h = h
+        self.info = PlanInfo3()
+        _check(L.fio3_plan_info(h, ctypes.byref(self.info)))
+        self.N, self.q = N, q
+        self.dtype = torch.complex128
+
+    def close(self) -> None:
+        if self._h is not None and _lib is not None:
+            _lib.fio3_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, x: torch.Tensor, name: str) -> torch.Tensor:
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.complex128:
+            raise TypeError("%s must be a complex128 CUDA tensor" % name)
+        if x.dim() == 3:
+            x = x.unsqueeze(0)
+        if tuple(x.shape[-3:]) != (self.N,) * 3:
+            raise ValueError("%s must have shape (nrhs, %d, %d, %d)" % ((name,) + (self.N,) * 3))
+        return x.contiguous()
+
+    def apply(self, f: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """u = B f (fio3_apply)."""
+        f = self._dev(f, "f")
+        u = torch.empty_like(f) if out is None else out
+        _check(lib().fio3_apply(self._h, f.data_ptr(), u.data_ptr(), f.shape[0], _stream_ptr(stream)))
+        return u
+
+    def adjoint(self, g: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """fbar = B^H g (fio3_apply_adjoint)."""
+        g = self._dev(g, "g")
+        fb = torch.empty_like(g) if out is None else out
+        _check(lib().fio3_apply_adjoint(self._h, g.data_ptr(), fb.data_ptr(), g.shape[0], _stream_ptr(stream)))
+        return fb
 
 
 class Batch:
