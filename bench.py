@@ -148,23 +148,27 @@ def kernel_flops_bytes(kind: str, info, nrhs: int) -> tuple[float, float]:
 
 
 def _tensor_switch(kind: str, switch_impl: int) -> bool:
-    return kind.startswith("switch") and switch_impl in (1, 3)
+    return kind.startswith("switch") and switch_impl in (1, 3, 4)
 
 
-def kernel_report(prof: dict, info, steps: int, switch_impl: int) -> tuple[dict, dict]:
+def kernel_report(prof: dict, info, steps: int, switch_impl: int, tf32_peak=None) -> tuple[dict, dict]:
     """Per-kernel breakdown of the timed applies and the dominant kernel's roofline.
 
     prof: {kernel kind: (launches, total ms)} over `steps` applies of the headline plan (`info`
     its PlanInfo).  Each kernel's fraction is its algorithmic work per launch over its average
     CUDA-event duration, against the peak of the pipe it runs on: the FP32 FMA peak, or for a
     tensor-core switch the TF32 peak (8 q^4 flops per pair and RHS, the split-TF32 products
-    counted once)."""
+    counted once); tf32_peak (flop/s): the measured tensor-core TF32 rate (fio_peak_probe), else
+    the bf16 figure of MEASURED_PEAKS.json times the nominal TF32/BF16 ratio."""
+    p_tf32 = tf32_peak if tf32_peak else TF32_PEAK_FROM_BF16 * 1e12
+    tf32_src = ("tcgen05.mma kind::tf32 M=128 N=256 measured by fio_peak_probe (of measured)" if tf32_peak
+                else "measured bf16 burst x nominal TF32/BF16 1.1/2.25 (of measured)")
     kernels = {}
     for k, (n, ms) in prof.items():
         fl, by = kernel_flops_bytes(k, info, NRHS)
         avg = ms / n
         tc = _tensor_switch(k, switch_impl)
-        peak = TF32_PEAK_FROM_BF16 * 1e12 if tc else FP32_PEAK
+        peak = p_tf32 if tc else FP32_PEAK
         kernels[k] = {"launches": n, "ms_per_launch": round(avg, 3), "share": None,
                       "tflops": round(fl / (avg * 1e-3) / 1e12, 2), "pipe": "tf32 tensor" if tc else "fp32 fma",
                       "frac": round(fl / (avg * 1e-3) / peak, 3), "gbs": round(by / (avg * 1e-3) / 1e9, 1)}
@@ -175,14 +179,13 @@ def kernel_report(prof: dict, info, steps: int, switch_impl: int) -> tuple[dict,
     fl, by = kernel_flops_bytes(dom, info, NRHS)
     dom_ms = prof[dom][1] / prof[dom][0]
     tc = _tensor_switch(dom, switch_impl)
-    peak = TF32_PEAK_FROM_BF16 * 1e12 if tc else FP32_PEAK
+    peak = p_tf32 if tc else FP32_PEAK
     roof = {"kernel": dom, "bound": "tensor" if tc else "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12,
             "peak": peak / 1e12, "unit": "TFLOP/s", "frac": fl / (dom_ms * 1e-3) / peak,
             "traffic": MEASURED_TRAFFIC.get(dom) if (info.N, info.q, NRHS) == (1024, 9, 32) else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on a smaller "
                               "case, scaled by pairs x RHS",
-            "peak_source": ("measured bf16 burst x nominal TF32/BF16 1.1/2.25 (of measured)" if tc
-                            else FP32_PEAK_NOTE + " (derived, not measured)"),
+            "peak_source": tf32_src if tc else FP32_PEAK_NOTE + " (derived, not measured)",
             "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
             "hbm_achieved_gbs": by / (dom_ms * 1e-3) / 1e9}
     return kernels, roof
@@ -223,7 +226,8 @@ def apply_roofline(info, nrhs: int, ms_apply: float, probes: dict) -> dict:
     p32 = FP32_PEAK
     p64 = probes.get("fp64") if isinstance(probes.get("fp64"), float) else 1.06e12
     pmufu = probes.get("sfu") if isinstance(probes.get("sfu"), float) else 4.9e12
-    ptf32 = TF32_PEAK_FROM_BF16 * 1e12
+    t = probes.get("mma_tf32_n256")
+    ptf32 = t if isinstance(t, float) else TF32_PEAK_FROM_BF16 * 1e12
     bw = _hbm_peak_gbs() * 1e9
     terms = {"hbm_ms": B / bw * 1e3, "fp32_ms": F32 / p32 * 1e3, "tf32_ms": Ftc / ptf32 * 1e3,
              "mufu_ms": 2 * E / pmufu * 1e3, "fp64_ms": 0.0}
@@ -236,7 +240,9 @@ def apply_roofline(info, nrhs: int, ms_apply: float, probes: dict) -> dict:
             "t_fp64_phases_ms": round(t64, 1),
             "apply_frac_with_fp64_phases": round(max(t_roof, t64) / ms_apply, 4),
             "peaks": {"fp32_tflops": round(p32 / 1e12, 2), "fp32_source": "derived (152 x 128 x 2 x 2.07 GHz)",
-                      "tf32_tflops": round(ptf32 / 1e12, 1), "tf32_source": "measured bf16 x 1.1/2.25 (of measured)",
+                      "tf32_tflops": round(ptf32 / 1e12, 1),
+                      "tf32_source": ("tcgen05 kind::tf32 N=256 by fio_peak_probe (of measured)" if isinstance(t, float)
+                                      else "measured bf16 x 1.1/2.25 (of measured)"),
                       "hbm_gbs": round(bw / 1e9, 1), "hbm_source": "MEASURED_PEAKS.json (of measured)",
                       "mufu_per_s": pmufu, "fp64_flops": p64, "mufu_fp64_source": "fio_peak_probe on this GPU"}}
 
@@ -455,13 +461,15 @@ def run_ours(args, rank, world, dist):
     out32 = whole_job_rate(N * N * NRHS, ms32, world)
     out64 = whole_job_rate(N * N, ms64, world)
 
-    kernels, roof = kernel_report(prof, info, args.steps, switch_impl)
     probes = {}
-    for kind in ("fp32", "fp64", "sfu"):
+    for kind in ("fp32", "fp64", "sfu", "mma_tf32_n64", "mma_tf32_n256", "mma_bf16_n256"):
         try:
             probes[kind] = fio.peak_probe(kind)
         except Exception as ex:  # measurement aid only
             probes[kind] = str(ex)
+    tf32 = probes.get("mma_tf32_n256")
+    kernels, roof = kernel_report(prof, info, args.steps, switch_impl,
+                                  tf32_peak=tf32 if isinstance(tf32, float) else None)
     roof["apply"] = apply_roofline(info, NRHS, ms32, probes)
 
     base, xi, ref = cpu_baseline(F[0], NSAMPLE)
@@ -480,7 +488,7 @@ def run_ours(args, rank, world, dist):
         "clocks": clk.summary(),
         "cpu_baseline": base,
         "switch_kernel": ["fp32_fma", "tcgen05_tf32_smem_a", "fp32_fma_warp_specialised",
-                          "tcgen05_tf32_tmem_a"][switch_impl] + " (plan autotuner)",
+                          "tcgen05_tf32_tmem_a", "tcgen05_tf32_tmem_a_wide_n"][switch_impl] + " (plan autotuner)",
         "translation_rhs_subtile": trans_rs, "switch_rhs_tile": sw_tile,
         "peak_probes": probes,
         "uneven_batch": ub,

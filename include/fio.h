@@ -146,7 +146,9 @@ typedef struct {
                               0 = FP32 FMA (one pair per CTA), 1 = tensor cores (tcgen05,
                               split TF32, kernel matrix in shared memory), 2 = FP32 FMA,
                               warp-specialised and persistent, 3 = tensor cores with the
-                              kernel matrix in tensor memory (persistent, one CTA per SM) */
+                              kernel matrix in tensor memory (persistent, one CTA per SM),
+                              4 = as 3 with the split-TF32 products as two wide MMAs per
+                              K-step (N = 192 and N = 128) */
   int trans_rs;            /* FIO_F32, translations of the p-shape (recursion in p, eq. alg2b, and
                               the adjoint of the recursion in x): right-hand sides per subtile
                               (2, 4 or 8), or 32 for the register-tiled kernel (one RHS per lane,
@@ -167,7 +169,7 @@ int fio_plan_info(fio_plan_t plan, fio_plan_info_t *info);
 int fio_check(fio_plan_t plan, void *stream);
 
 /* fio_plan_set_wait_limit -- for tests of the failure path: the limit, in ns, of the
- * waits by which the tensor-memory switch kernel (switch_impl 3) hands chunks between
+ * waits by which the tensor-memory switch kernels (switch_impl 3, 4) hand chunks between
  * its producer warps and its MMA warp (0 restores the normal 2 s).  A tiny limit makes
  * those waits expire: the kernel then records the expiry, stops issuing work, still waits
  * with the normal limit for the tensor-core operations it issued, frees its tensor memory
@@ -177,7 +179,8 @@ int fio_plan_set_wait_limit(fio_plan_t plan, unsigned long long ns);
 
 /* fio_plan_set_switch -- override the autotuner's choice of the FIO_F32 switch
  * kernel: impl 0 = FP32 FMA, 1 = tensor cores (kernel matrix in shared memory),
- * 2 = warp-specialised FP32 FMA, 3 = tensor cores (kernel matrix in tensor memory).
+ * 2 = warp-specialised FP32 FMA, 3 = tensor cores (kernel matrix in tensor memory), 4 = as 3
+ * with two wide MMAs per K-step.
  * FIO_EINVAL if the plan is FIO_F64 or the kernel does not fit this plan (its
  * shared memory need: 1 and 2 are not available for every q). */
 int fio_plan_set_switch(fio_plan_t plan, int impl);
@@ -296,6 +299,10 @@ int fio_profile_read(fio_plan_t plan, fio_kernel_time_t *out, int max, int *n);
  * kind 0 FP32 FMA, 1 FP64 FMA (returned as flop/s, 2 per FMA), 2 FP32 sin/cos
  * through the special-function unit (results/s).  A fixed dependent-chain
  * kernel over every SM, timed with CUDA events; synchronises the device.
+ * kinds 3..8: the tensor-core rate (flop/s, 2 per multiply-add) of tcgen05.mma, M = 128,
+ * one CTA per SM issuing back to back with the operands rotating over 16 K-steps:
+ * A in tensor memory: 3 TF32 N = 64, 4 BF16 N = 64, 5 TF32 N = 256, 6 BF16 N = 256;
+ * A in shared memory: 7 TF32 N = 64, 8 BF16 N = 64.
  * The paper has no counterpart: it is a measurement aid for the roofline. */
 int fio_peak_probe(int kind, double *per_second);
 

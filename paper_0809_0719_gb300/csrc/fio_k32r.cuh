@@ -196,27 +196,27 @@ __device__ __forceinline__ void rp_sweep(float2 (&Y)[Q][Q], const float2 *pre, c
     stage_wait(bulk, &mbar[i1], 0, status);
 #pragma unroll 1
     for (int tp1 = 0; tp1 < Q; tp1++) {
-      float2 s[2][Q];
+      // z[t2] = sum_{i2, t'2} T^{i2}[t2][t'2] (pre (.) in)[i2][t'1][t'2]: the row is streamed
+      // one element at a time into q independent accumulators
+      float2 z[Q];
+#pragma unroll
+      for (int t2 = 0; t2 < Q; t2++) z[t2] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i2 = 0; i2 < 2; i2++)
 #pragma unroll
         for (int tp2 = 0; tp2 < Q; tp2++) {
           const int i = 2 * i1 + i2;
-          s[i2][tp2] = cmul(pre[i * Q2 + tp1 * Q + tp2], in_s[(i * kRT + rr) * Q2 + tp1 * Q + tp2]);
+          const float2 sv = cmul(pre[i * Q2 + tp1 * Q + tp2], in_s[(i * kRT + rr) * Q2 + tp1 * Q + tp2]);
+#pragma unroll
+          for (int t2 = 0; t2 < Q; t2++) z[t2] = fma2s(tm.T[i2][t2][tp2], sv, z[t2]);
         }
       float tc[Q];
 #pragma unroll
       for (int t1 = 0; t1 < Q; t1++) tc[t1] = tT[(i1 * Q + tp1) * Q + t1];
 #pragma unroll
-      for (int t2 = 0; t2 < Q; t2++) {
-        float2 z = make_float2(0.f, 0.f);
+      for (int t2 = 0; t2 < Q; t2++)
 #pragma unroll
-        for (int i2 = 0; i2 < 2; i2++)
-#pragma unroll
-          for (int tp2 = 0; tp2 < Q; tp2++) z = fma2s(tm.T[i2][t2][tp2], s[i2][tp2], z);
-#pragma unroll
-        for (int t1 = 0; t1 < Q; t1++) Y[t1][t2] = fma2s(tc[t1], z, Y[t1][t2]);
-      }
+        for (int t1 = 0; t1 < Q; t1++) Y[t1][t2] = fma2s(tc[t1], z[t2], Y[t1][t2]);
     }
   }
 }
@@ -294,16 +294,17 @@ __device__ __forceinline__ void rx_pass_b(float2 (&acc)[Q][Q], const float2 *wro
   const int o = rev ? Q - 1 : 0, st = rev ? -1 : 1;
 #pragma unroll
   for (int t1 = 0; t1 < Q; t1++) {
-    float2 w[Q];
+    float2 v[Q];  // q independent accumulators, the W row streamed one element at a time
 #pragma unroll
-    for (int tp2 = 0; tp2 < Q; tp2++) w[tp2] = wrow[t1 * Q + o + st * tp2];
+    for (int t2 = 0; t2 < Q; t2++) v[t2] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int t2 = 0; t2 < Q; t2++) {
-      float2 v = make_float2(0.f, 0.f);
+    for (int tp2 = 0; tp2 < Q; tp2++) {
+      const float2 w = wrow[t1 * Q + o + st * tp2];
 #pragma unroll
-      for (int tp2 = 0; tp2 < Q; tp2++) v = fma2s(tm.T[1][tp2][t2], w[tp2], v);
-      acc[t1][t2] = cmac(post[t1 * Q + o + st * t2], v, acc[t1][t2]);
+      for (int t2 = 0; t2 < Q; t2++) v[t2] = fma2s(tm.T[1][tp2][t2], w, v[t2]);
     }
+#pragma unroll
+    for (int t2 = 0; t2 < Q; t2++) acc[t1][t2] = cmac(post[t1 * Q + o + st * t2], v[t2], acc[t1][t2]);
   }
 }
 
@@ -364,28 +365,27 @@ __global__ void __launch_bounds__(4 * kRT, 2)
     // task (t'2, k1) per warp, RHS per lane
     for (int c = j; c < 2 * Q; c += 4) {
       const int tp2 = c >> 1, k1 = c & 1;
-      float2 col[Q];
+      float2 a[Q];  // W[k1][r][t1][t'2] for every t1, the column streamed one element at a time
 #pragma unroll
-      for (int tp1 = 0; tp1 < Q; tp1++)
-        col[tp1] = cmul(pre_s[i * Q2 + tp1 * Q + tp2], slot[rr * Q2 + tp1 * Q + tp2]);
+      for (int t1 = 0; t1 < Q; t1++) a[t1] = make_float2(0.f, 0.f);
       float2 *wcol = W + (k1 * kRT + r) * Q2 + tp2;
       if (k1 == 0) {
 #pragma unroll
-        for (int t1 = 0; t1 < Q; t1++) {
-          float2 a = make_float2(0.f, 0.f);
+        for (int tp1 = 0; tp1 < Q; tp1++) {
+          const float2 sv = cmul(pre_s[i * Q2 + tp1 * Q + tp2], slot[rr * Q2 + tp1 * Q + tp2]);
 #pragma unroll
-          for (int tp1 = 0; tp1 < Q; tp1++) a = fma2s(tm.T[0][tp1][t1], col[tp1], a);
-          wcol[t1 * Q] = a;
+          for (int t1 = 0; t1 < Q; t1++) a[t1] = fma2s(tm.T[0][tp1][t1], sv, a[t1]);
         }
       } else {
 #pragma unroll
-        for (int t1 = 0; t1 < Q; t1++) {
-          float2 a = make_float2(0.f, 0.f);
+        for (int tp1 = 0; tp1 < Q; tp1++) {
+          const float2 sv = cmul(pre_s[i * Q2 + tp1 * Q + tp2], slot[rr * Q2 + tp1 * Q + tp2]);
 #pragma unroll
-          for (int tp1 = 0; tp1 < Q; tp1++) a = fma2s(tm.T[1][tp1][t1], col[tp1], a);
-          wcol[t1 * Q] = a;
+          for (int t1 = 0; t1 < Q; t1++) a[t1] = fma2s(tm.T[1][tp1][t1], sv, a[t1]);
         }
       }
+#pragma unroll
+      for (int t1 = 0; t1 < Q; t1++) wcol[t1 * Q] = a[t1];
     }
     __syncthreads();  // W complete; slot i & 1 no longer read
     if (i + 2 < 4) {

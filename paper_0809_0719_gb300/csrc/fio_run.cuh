@@ -38,7 +38,8 @@ struct PlanDev {
   int smem_optin;
   int num_sms;
   int switch_impl;  // FP32 switch: 0 FFMA, 1 tensor cores (A in smem), 2 warp-specialised FFMA,
-                    // 3 tensor cores (A in tensor memory); chosen by the plan's autotuner
+                    // 3 tensor cores (A in tensor memory), 4 as 3 with two wide MMAs per K-step;
+                    // chosen by the plan's autotuner
   int trans_rs;     // FP32 translations of the p-shape (recursion in p, adjoint of the recursion
                     // in x): RHS per subtile 2, 4 or 8, or 32 for the register-tiled kernels
                     // (fio_k32r.cuh, q <= 9); chosen by the plan's autotuner
@@ -204,15 +205,16 @@ template <typename R, int Q> struct Runner {
         k<<<grid, SwWs<Q>::threads, SwWs<Q>::smem, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, nwork);
         return check();
       }
-      const size_t smem_tm = TmShape<Q>::smem_bytes();
-      if (fast32() && p.switch_impl == 3 && p.status && smem_tm <= (size_t)p.smem_optin) {
+      const bool wide = p.switch_impl == 4;
+      const size_t smem_tm = wide ? TmShape<Q, true>::smem_bytes() : TmShape<Q>::smem_bytes();
+      if (fast32() && (p.switch_impl == 3 || wide) && p.status && smem_tm <= (size_t)p.smem_optin) {
         const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
         const Geom g = geom(p.lm, kRMax, 1, pairs);
         const long long nsu = pairs >> (p.L - p.lm);  // (box A, angular box) super-units
         dim3 grid((unsigned)std::min<long long>(nsu, std::max(1, p.num_sms)), (unsigned)((nrhs + kRMax - 1) / kRMax));
         if (count_only) return check();
         pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
-        auto k = k32_switch_tm<Q, FWD>;
+        auto k = wide ? k32_switch_tm<Q, FWD, true> : k32_switch_tm<Q, FWD, false>;
         set_smem(k, p.smem_optin);
         k<<<grid, kTmThreads, smem_tm, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, p.status,
                                              p.handoff_ns);
@@ -410,6 +412,8 @@ template <typename R, int Q> struct Runner {
       if (p.status && TcShape<Q>::smem_bytes() <= (size_t)p.smem_optin) m |= 2;
       if (SwWs<Q>::smem <= p.smem_optin) m |= 4;
       if (p.status && TmShape<Q>::smem_bytes() <= (size_t)p.smem_optin && (1 << (p.L - p.lm)) <= kTmNb1Max) m |= 8;
+      if (p.status && TmShape<Q, true>::smem_bytes() <= (size_t)p.smem_optin && (1 << (p.L - p.lm)) <= kTmNb1Max)
+        m |= 16;
       return m;
     }
   }
@@ -467,7 +471,7 @@ template <typename R, int Q> struct Runner {
       const int avail = switch_impls();
       float best = 1e30f;
       int pick = 0, pick_rb = 4;
-      for (int impl = 0; impl < 4; impl++) {
+      for (int impl = 0; impl < 5; impl++) {
         if (!(avail >> impl & 1)) continue;
         for (int rb : {4, 8}) {
           if (impl != 0 && rb != 4) continue;  // only the one-pair-per-CTA kernel has both tiles

@@ -416,25 +416,49 @@ constexpr int kTmDcols = 128;                   // two accumulators of 64 column
 constexpr int kTmAcols = 2 * kTmKC;             // TMEM columns of one A slot (two TF32 parts)
 constexpr int kTmSmemFloor = 120 * 1024;        // > half an SM's shared memory: one CTA (512 TMEM columns) per SM
 constexpr int kTmNb1Max = 64;                   // radial boxes at the switch level (2^ceil(L/2), N <= 4096)
-static_assert(kTmDcols + kTmNB * kTmAcols <= 512, "tensor memory budget");
 constexpr int kTmPQ = kTmProducers / 128;        // producer warps per lane quarter
-static_assert(kTmProducers % 128 == 0 && (kTmKC / 2) % kTmPQ == 0, "producer warps split a chunk's columns evenly");
+static_assert(kTmProducers % 128 == 0, "producer warps per lane quarter");
 
-template <int Q> struct TmShape {
+// W (wide): the split-TF32 products as two wide MMAs per K-step, A0 x [B0|B1|B2] (N = 192)
+// and A1 x [B0|B1] (N = 128), into two double-buffered 192-column accumulators whose three
+// 64-column blocks the epilogue sums; tensor memory then holds two A slots of 4 K-steps.
+template <bool W> struct TmCfg {
+  static constexpr int CK = W ? 4 : kTmCK;         // MMA K-steps per chunk
+  static constexpr int KC = 8 * CK;                // K columns per chunk
+  static constexpr int NB = W ? 2 : kTmNB;         // ring slots
+  static constexpr int ACC = W ? 192 : 64;         // columns of one accumulator
+  static constexpr int DC = 2 * ACC;               // both accumulators
+  static constexpr int AC = 2 * KC;                // one A slot (two TF32 parts)
+  static_assert(DC + NB * AC <= 512, "tensor memory budget");
+  static_assert((KC / 2) % kTmPQ == 0, "producer warps split a chunk's columns evenly");
+};
+
+template <int Q, bool W = false> struct TmShape {
+  typedef TmCfg<W> C;
   static constexpr int Q2 = Q * Q;
   static constexpr int KP = ((2 * Q2 + 7) / 8) * 8;        // padded K
   static constexpr int KS = KP / 8;                        // MMA K-steps per pair
-  static constexpr int NCH = (KS + kTmCK - 1) / kTmCK;     // chunks per pair (the last may be partial)
-  static constexpr int B_FLOATS = 64 * kTmKC;              // one TF32 part of one B slot
-  static constexpr size_t b_bytes = (size_t)kTmNB * kTcPB * B_FLOATS * 4;
+  static constexpr int NCH = (KS + C::CK - 1) / C::CK;     // chunks per pair (the last may be partial)
+  static constexpr int B_FLOATS = 64 * C::KC;              // one TF32 part of one B slot
+  static constexpr size_t b_bytes = (size_t)C::NB * kTcPB * B_FLOATS * 4;
   static constexpr size_t in_bytes = (size_t)2 * kRMax * Q2 * 8;
   static constexpr size_t gt_bytes = (size_t)2 * Q2 * Q * sizeof(df);
   static constexpr size_t rho_bytes = (size_t)kTmNb1Max * Q * sizeof(df);
-  static constexpr int nbar = 2 * kTmNB + 7;
+  static constexpr int nbar = 2 * C::NB + 7;
   static constexpr size_t used = b_bytes + in_bytes + gt_bytes + rho_bytes + nbar * 8 + 16;
   static constexpr size_t smem_bytes() { return used > (size_t)kTmSmemFloor ? used : (size_t)kTmSmemFloor; }
 };
 
+// Instruction descriptor of kind::tf32: D f32, A and B tf32 K-major, M = 128, N as given.
+template <int N> constexpr uint32_t tf32_idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+}
+template <int N> __device__ __forceinline__ void tm_mma_n(uint32_t dtm, uint32_t atm, uint64_t db, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
+      "r"(atm), "l"(db), "r"(tf32_idesc<N>()), "r"(acc));
+}
 __device__ __forceinline__ void tm_mma(uint32_t dtm, uint32_t atm, uint64_t db, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -482,24 +506,25 @@ __device__ __forceinline__ void tm_arrive(uint64_t *mbar) { mbar_arrive(mbar); }
 // handoff_ns: limit of the waits between the producer warps and the MMA warp (0: the
 // normal 2 s); a test sets it tiny to make them expire.  The final drain of the issued
 // MMAs (fin) always waits with the normal limit.
-template <int Q, bool FWD>
+template <int Q, bool FWD, bool W = false>
 __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, TablesF tf, Phase ph, Geom g,
                                                                 const float2 *__restrict__ in,
                                                                 float2 *__restrict__ out, int *status,
                                                                 unsigned long long handoff_ns) {
-  typedef TmShape<Q> S;
+  typedef TmShape<Q, W> S;
+  typedef TmCfg<W> C;
   constexpr int Q2 = S::Q2, KS = S::KS, NCH = S::NCH;
-  constexpr int CPW = kTmKC / 2 / kTmPQ;  // complex kernel columns per producer warp and chunk
+  constexpr int CPW = C::KC / 2 / kTmPQ;  // complex kernel columns per producer warp and chunk
   constexpr int RPW = kRMax / kTmPQ;      // RHS per producer warp in the epilogue
-  constexpr int KCC = kTmKC / 4;  // core-matrix columns (4 K each) per chunk
+  constexpr int KCC = C::KC / 4;  // core-matrix columns (4 K each) per chunk
   extern __shared__ __align__(16) unsigned char smem_raw[];  // no-swizzle operands need 16-byte alignment
   float *bs = (float *)smem_raw;                                   // B [slot][part][8 row groups][KCC][8][4]
   float2 *instage = (float2 *)(smem_raw + S::b_bytes);             // [2][kRMax][Q2] coefficients
   df *gt = (df *)(smem_raw + S::b_bytes + S::in_bytes);            // [2][Q2][Q] G(x_t, p2_s2)
   df *rho = gt + 2 * Q2 * Q;                                       // [kTmNb1Max][Q] rho of every radial box
   uint64_t *full = (uint64_t *)(rho + kTmNb1Max * Q);
-  uint64_t *fre = full + kTmNB;
-  uint64_t *dfull = fre + kTmNB;
+  uint64_t *fre = full + C::NB;
+  uint64_t *dfull = fre + C::NB;
   uint64_t *dempty = dfull + 2;
   uint64_t *tab = dempty + 2;
   uint64_t *fin = tab + 2;
@@ -527,7 +552,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
 
   if (tid == 0) {
     for (int b = 0; b < S::nbar; b++) {
-      const int cnt = (b < kTmNB || (b >= 2 * kTmNB + 2 && b < 2 * kTmNB + 6)) ? kTmProducers : 1;
+      const int cnt = (b < C::NB || (b >= 2 * C::NB + 2 && b < 2 * C::NB + 6)) ? kTmProducers : 1;
       const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&full[b]);
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(cnt));
     }
@@ -565,25 +590,30 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
       const int d = (int)(k & 1);
       if (k >= 2 && !waitw(&dempty[d], (uint32_t)((k >> 1) - 1) & 1)) break;  // read-out of pair k - 2
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dtm = tmem + 64 * d;
+      const uint32_t dtm = tmem + C::ACC * d;
       for (int c = 0; c < NCH; c++, gc++) {
-        const int j = (int)(gc % kTmNB);
-        if (!waitw(&full[j], (gc / kTmNB) & 1)) { live = false; break; }
+        const int j = (int)(gc % C::NB);
+        if (!waitw(&full[j], (gc / C::NB) & 1)) { live = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (lane == 0) {
-          const int nks = min(kTmCK, KS - c * kTmCK);
-          const uint32_t a0 = tmem + kTmDcols + j * kTmAcols;
+          const int nks = min(C::CK, KS - c * C::CK);
+          const uint32_t a0 = tmem + C::DC + j * C::AC;
           for (int ks = 0; ks < nks; ks++) {
             uint64_t dB[kTcPB];
 #pragma unroll
             for (int q_ = 0; q_ < kTcPB; q_++)
               dB[q_] = tc_desc(aB + ((j * kTcPB + q_) * S::B_FLOATS) * 4 + ks * 256, 128, sbo);
-            const uint32_t ta0 = a0 + 8 * ks, ta1 = a0 + kTmKC + 8 * ks;
-            tm_mma(dtm, ta0, dB[0], (c > 0 || ks > 0) ? 1u : 0u);
-            tm_mma(dtm, ta0, dB[1], 1u);
-            tm_mma(dtm, ta1, dB[0], 1u);
-            tm_mma(dtm, ta0, dB[2], 1u);
-            tm_mma(dtm, ta1, dB[1], 1u);
+            const uint32_t ta0 = a0 + 8 * ks, ta1 = a0 + C::KC + 8 * ks;
+            if (W) {  // the B parts lie one after another: one descriptor spans 192 or 128 rows
+              tm_mma_n<192>(dtm, ta0, dB[0], (c > 0 || ks > 0) ? 1u : 0u);
+              tm_mma_n<128>(dtm, ta1, dB[0], 1u);
+            } else {
+              tm_mma(dtm, ta0, dB[0], (c > 0 || ks > 0) ? 1u : 0u);
+              tm_mma(dtm, ta0, dB[1], 1u);
+              tm_mma(dtm, ta1, dB[0], 1u);
+              tm_mma(dtm, ta0, dB[2], 1u);
+              tm_mma(dtm, ta1, dB[1], 1u);
+            }
           }
           tc_commit(&fre[j]);
           if (c == NCH - 1) tc_commit(&dfull[d]);
@@ -642,10 +672,23 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (arows) {
         static_assert(RPW == 8, "epilogue reads 8 columns per warp");
-        const uint32_t trow = tmem + 64 * d + RPW * wh + ((uint32_t)(32 * qd) << 16);
+        const uint32_t trow = tmem + C::ACC * d + RPW * wh + ((uint32_t)(32 * qd) << 16);
         float re[RPW], im[RPW];
         tc_ld8(trow, re);
         tc_ld8(trow + 32, im);
+        if (W) {  // the A0 B1 + A1 B1 and A0 B2 blocks of the wide accumulator, added in order
+#pragma unroll
+          for (int blk = 1; blk < 3; blk++) {
+            float re2[RPW], im2[RPW];
+            tc_ld8(trow + 64 * blk, re2);
+            tc_ld8(trow + 64 * blk + 32, im2);
+#pragma unroll
+            for (int r = 0; r < RPW; r++) {
+              re[r] += re2[r];
+              im[r] += im2[r];
+            }
+          }
+        }
         if (o < Q2) {
           float2 *dst = out + pair_of(k) * nrq + (long long)(r0 + RPW * wh) * Q2 + o;
 #pragma unroll
@@ -689,15 +732,15 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
       const df rho_row = (!FWD && !sep) ? rhob[oc / Q] : df{0.f, 0.f};
       const df *grow = FWD ? gtb + oc * Q : gtb + oc % Q;
       for (int c = 0; c < NCH; c++, gc++) {
-        const int j = (int)(gc % kTmNB);
-        if (gc >= kTmNB && !waitw(&fre[j], (gc / kTmNB - 1) & 1)) { live = false; break; }
+        const int j = (int)(gc % C::NB);
+        if (gc >= C::NB && !waitw(&fre[j], (gc / C::NB - 1) & 1)) { live = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // A: this lane's row, CPW complex columns, both TF32 parts, into tensor memory.  The
         // fast path is branch-free (indices clamped, invalid entries selected to zero) so the
         // CPW independent phase chains interleave.
         if (arows) {
           float p0[2 * CPW], p1[2 * CPW];
-          const int i0 = c * (kTmKC / 2) + wh * CPW;  // first column of this warp
+          const int i0 = c * (C::KC / 2) + wh * CPW;  // first column of this warp
 #pragma unroll
           for (int kk = 0; kk < CPW; kk++) {
             const int i = i0 + kk;
@@ -736,9 +779,9 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
             p1[2 * kk + 1] = pi_[1];
           }
           __syncwarp();
-          const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + kTmDcols + j * kTmAcols + 2 * CPW * wh;
+          const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + C::DC + j * C::AC + 2 * CPW * wh;
           tm_st<2 * CPW>(ta, p0);
-          tm_st<2 * CPW>(ta + kTmKC, p1);
+          tm_st<2 * CPW>(ta + C::KC, p1);
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
         // B: lane r builds rows r and 32 + r of core-matrix column kc from X[r][s0], X[r][s0+1]
@@ -746,7 +789,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
         if (bidx >= 0) {
           float *cb = bs + j * kTcPB * S::B_FLOATS;
           for (int kc = bidx; kc < KCC; kc += bstride) {
-            const int s0 = c * (kTmKC / 2) + 2 * kc;
+            const int s0 = c * (C::KC / 2) + 2 * kc;
             const int rr = lane < rc ? lane : 0;
             float2 x0 = ins[rr * Q2 + min(s0, Q2 - 1)], x1 = ins[rr * Q2 + min(s0 + 1, Q2 - 1)];
             if (!(lane < rc && s0 < Q2)) x0 = make_float2(0.f, 0.f);  // rows beyond rc were not loaded

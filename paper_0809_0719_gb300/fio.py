@@ -224,7 +224,8 @@ class Plan:
     def set_switch(self, impl: int) -> None:
         """fio_plan_set_switch: 0 = FP32 FMA switch kernel, 1 = tensor-core switch kernel
         (kernel matrix in shared memory), 2 = warp-specialised persistent FP32 FMA switch
-        kernel, 3 = tensor-core switch kernel with the kernel matrix in tensor memory."""
+        kernel, 3 = tensor-core switch kernel with the kernel matrix in tensor memory, 4 = as 3 with
+        two wide MMAs per K-step."""
         _check(lib().fio_plan_set_switch(self._h, int(impl)))
         self.info.switch_impl = int(impl)
 
@@ -470,7 +471,9 @@ def apply_wave_series(plan: Plan, times, x: torch.Tensor, out: torch.Tensor | No
 def peak_probe(kind: str) -> float:
     """fio_peak_probe on the current device: 'fp32' / 'fp64' flop/s or 'sfu' sin/s."""
     v = ctypes.c_double()
-    _check(lib().fio_peak_probe({"fp32": 0, "fp64": 1, "sfu": 2}[kind], ctypes.byref(v)))
+    kinds = {"fp32": 0, "fp64": 1, "sfu": 2, "mma_tf32_n64": 3, "mma_bf16_n64": 4, "mma_tf32_n256": 5,
+             "mma_bf16_n256": 6, "mma_tf32_n64_smem_a": 7, "mma_bf16_n64_smem_a": 8}
+    _check(lib().fio_peak_probe(kinds[kind], ctypes.byref(v)))
     return float(v.value)
 
 
