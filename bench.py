@@ -119,7 +119,7 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch at the N=1024, q=9, 32-RHS workload, from ncu captures of
 # the current kernels on smaller cases (inputs larger than L2), scaled by pairs x RHS.
-MEASURED_TRAFFIC = {"switch": 171.0e9, "trans_p": 172.3e9, "trans_x": 172.4e9, "init": 86.7e9, "term": 87.2e9}
+MEASURED_TRAFFIC = {"switch": 171.0e9, "trans_p": 173.1e9, "trans_x": 173.1e9, "init": 86.7e9, "term": 87.2e9}
 
 
 def kernel_flops_bytes(kind: str, info, nrhs: int) -> tuple[float, float]:
@@ -155,39 +155,55 @@ def kernel_report(prof: dict, info, steps: int, switch_impl: int, tf32_peak=None
     """Per-kernel breakdown of the timed applies and the dominant kernel's roofline.
 
     prof: {kernel kind: (launches, total ms)} over `steps` applies of the headline plan (`info`
-    its PlanInfo).  Each kernel's fraction is its algorithmic work per launch over its average
-    CUDA-event duration, against the peak of the pipe it runs on: the FP32 FMA peak, or for a
-    tensor-core switch the TF32 peak (8 q^4 flops per pair and RHS, the split-TF32 products
-    counted once); tf32_peak (flop/s): the measured tensor-core TF32 rate (fio_peak_probe), else
-    the bf16 figure of MEASURED_PEAKS.json times the nominal TF32/BF16 ratio."""
+    its PlanInfo).  Each kernel's roofline time is the larger of its algorithmic work at the
+    peak of the pipe it runs on (the FP32 FMA peak, or for a tensor-core switch the TF32 peak:
+    8 q^4 flops per pair and RHS, the split-TF32 products counted once) and its algorithmic
+    HBM bytes at the measured HBM bandwidth; `bound` names the larger, and frac = roofline time
+    / measured time (equivalently achieved / peak in the bound's unit).  tf32_peak (flop/s):
+    the measured tensor-core TF32 rate (fio_peak_probe), else the bf16 figure of
+    MEASURED_PEAKS.json times the nominal TF32/BF16 ratio."""
     p_tf32 = tf32_peak if tf32_peak else TF32_PEAK_FROM_BF16 * 1e12
     tf32_src = ("tcgen05.mma kind::tf32 M=128 N=256 measured by fio_peak_probe (of measured)" if tf32_peak
                 else "measured bf16 burst x nominal TF32/BF16 1.1/2.25 (of measured)")
-    kernels = {}
-    for k, (n, ms) in prof.items():
+    bw = _hbm_peak_gbs() * 1e9
+
+    def roof_of(k, avg_ms):
         fl, by = kernel_flops_bytes(k, info, NRHS)
-        avg = ms / n
         tc = _tensor_switch(k, switch_impl)
         peak = p_tf32 if tc else FP32_PEAK
-        kernels[k] = {"launches": n, "ms_per_launch": round(avg, 3), "share": None,
-                      "tflops": round(fl / (avg * 1e-3) / 1e12, 2), "pipe": "tf32 tensor" if tc else "fp32 fma",
-                      "frac": round(fl / (avg * 1e-3) / peak, 3), "gbs": round(by / (avg * 1e-3) / 1e9, 1)}
+        t_c, t_m = fl / peak, by / bw
+        hbm = t_m > t_c
+        sec = avg_ms * 1e-3
+        return {"bound": "hbm" if hbm else ("tensor" if tc else "alu"),
+                "achieved": (by / sec / 1e9) if hbm else (fl / sec / 1e12),
+                "peak": (bw / 1e9) if hbm else (peak / 1e12), "unit": "GB/s" if hbm else "TFLOP/s",
+                "frac": max(t_c, t_m) / sec, "t_compute_ms": t_c * 1e3, "t_hbm_ms": t_m * 1e3,
+                "pipe": "tf32 tensor" if tc else "fp32 fma", "fl": fl, "by": by}
+
+    kernels = {}
+    for k, (n, ms) in prof.items():
+        avg = ms / n
+        r = roof_of(k, avg)
+        kernels[k] = {"launches": n, "ms_per_launch": round(avg, 3), "share": None, "bound": r["bound"],
+                      "frac": round(r["frac"], 3), "tflops": round(r["fl"] / (avg * 1e-3) / 1e12, 2),
+                      "gbs": round(r["by"] / (avg * 1e-3) / 1e9, 1), "pipe": r["pipe"]}
     tot = sum(v["ms_per_launch"] * v["launches"] for v in kernels.values())
     for v in kernels.values():
         v["share"] = round(v["ms_per_launch"] * v["launches"] / tot, 3)
     dom = max(kernels, key=lambda k: kernels[k]["share"])
-    fl, by = kernel_flops_bytes(dom, info, NRHS)
     dom_ms = prof[dom][1] / prof[dom][0]
-    tc = _tensor_switch(dom, switch_impl)
-    peak = p_tf32 if tc else FP32_PEAK
-    roof = {"kernel": dom, "bound": "tensor" if tc else "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12,
-            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": fl / (dom_ms * 1e-3) / peak,
+    r = roof_of(dom, dom_ms)
+    roof = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"],
+            "frac": r["frac"],
             "traffic": MEASURED_TRAFFIC.get(dom) if (info.N, info.q, NRHS) == (1024, 9, 32) else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on a smaller "
                               "case, scaled by pairs x RHS",
-            "peak_source": tf32_src if tc else FP32_PEAK_NOTE + " (derived, not measured)",
-            "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
-            "hbm_achieved_gbs": by / (dom_ms * 1e-3) / 1e9}
+            "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if r["bound"] == "hbm"
+                            else tf32_src if r["pipe"] == "tf32 tensor" else FP32_PEAK_NOTE + " (derived, not measured)"),
+            "t_compute_ms": r["t_compute_ms"], "t_hbm_ms": r["t_hbm_ms"],
+            "algorithmic_flops_per_launch": r["fl"], "algorithmic_bytes_per_launch": r["by"],
+            "compute_pipe": r["pipe"], "compute_achieved_tflops": r["fl"] / (dom_ms * 1e-3) / 1e12,
+            "hbm_achieved_gbs": r["by"] / (dom_ms * 1e-3) / 1e9}
     return kernels, roof
 
 

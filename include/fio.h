@@ -346,7 +346,8 @@ int fio_apply_noalloc(int N, int q, int phase_id, const double *params, int npar
  * of different q (or s) form separate groups whose launch chains run on
  * parallel branches of the graph.  Each plan's results are bit-identical to
  * fio_apply / fio_apply_adjoint on that plan alone with the FP32 FMA switch
- * (switch_impl 0); the batch never uses the tensor-core switch.
+ * (switch_impl 0) and the RHS-subtile translations (trans_rs, trans_rs_x 2, 4 or 8):
+ * the batch uses neither the tensor-core switch nor the register-tiled translations.
  *
  * Data: one packed DEVICE buffer for all inputs and one for all outputs.  Plan i
  * occupies elements [off[i], off[i+1]) of both (complex64), laid out as

@@ -23,18 +23,28 @@ def test_kernel_report(switch_impl):
     kernels, roof = bench.kernel_report(PROF, INFO, 2, switch_impl)
     assert sum(v["share"] for v in kernels.values()) == pytest.approx(1.0, abs=2e-3)
     assert roof["kernel"] == "trans_x"  # 352.8 ms of 1135.7: the largest share
-    fl, _ = bench.kernel_flops_bytes("trans_x", INFO, bench.NRHS)
-    # 24 q^3 + 30 q^2 flops per pair and RHS, 4 Mi pairs, 32 RHS
+    fl, by = bench.kernel_flops_bytes("trans_x", INFO, bench.NRHS)
+    # 24 q^3 + 30 q^2 flops per pair and RHS, 4 Mi pairs, 32 RHS; the state read and written once
     assert fl == (24 * 729 + 30 * 81) * INFO.pairs_per_level * 32
+    assert by == 2 * INFO.pairs_per_level * 32 * 81 * 8
+    # compute-bound: 2.67e12 flops at the FP32 peak (33 ms) exceed 174 GB at the HBM peak (26 ms)
+    assert roof["bound"] == "alu"
     assert roof["achieved"] == pytest.approx(fl / 88.2e-3 / 1e12)
     assert roof["frac"] == pytest.approx(roof["achieved"] * 1e12 / bench.FP32_PEAK)
-    assert roof["bound"] == "alu"
     assert roof["traffic"] == bench.MEASURED_TRAFFIC["trans_x"]
+    # the switch: 8 q^4 flops per pair and RHS are 7.0e12, ~6 ms at a TF32 peak (then its 174 GB of
+    # state, 26 ms at the HBM peak, bound it) but 87 ms on the FP32 FMA pipe
     sw = kernels["switch"]
     swfl = 8 * 9 ** 4 * INFO.pairs_per_level * 32
-    peak = bench.TF32_PEAK_FROM_BF16 * 1e12 if switch_impl == 3 else bench.FP32_PEAK
-    assert sw["frac"] == pytest.approx(swfl / 158.4e-3 / peak, abs=1e-3)
+    if switch_impl == 3:
+        assert sw["bound"] == "hbm"
+        assert sw["frac"] == pytest.approx(by / (bench._hbm_peak_gbs() * 1e9) / 158.4e-3, abs=1e-3)
+    else:
+        assert sw["bound"] == "alu"
+        assert sw["frac"] == pytest.approx(swfl / bench.FP32_PEAK / 158.4e-3, abs=1e-3)
     assert sw["pipe"] == ("tf32 tensor" if switch_impl == 3 else "fp32 fma")
+    # init and term move 87 GB (13 ms) against 0.7-0.8e12 flops (9-10 ms): HBM-bound too
+    assert kernels["init"]["bound"] == "hbm" and kernels["term"]["bound"] == "hbm"
 
 
 def test_apply_roofline_by_hand():

@@ -2,7 +2,8 @@
 (q, s) group, replayed from captured CUDA graphs.
 
 * every plan's slice of a batched apply (forward and adjoint) equals, bit for bit,
-  fio_apply / fio_apply_adjoint of that plan alone with the FP32 FMA switch: the
+  fio_apply / fio_apply_adjoint of that plan alone with the FP32 FMA switch and the
+  RHS-subtile translations (the kernels a batch runs): the
   batched kernels run the same per-unit code, only the assignment of units to
   CTAs differs;
 * the uneven-batch workload (96 plans, N in {64..512}, q in {5, 7, 9}, 1-8 RHS,
@@ -38,10 +39,12 @@ def fio():
 
 
 def _plans(fio, specs):
+    # the kernels a batch runs: the FFMA switch and the RHS-subtile translations (a plan alone
+    # may otherwise be tuned to the register-tiled translations, which sum in another order)
     plans = []
     for N, q, phase, nrhs in specs:
         p = fio.Plan(N, q, phase, PARAMS[phase], "f32", nrhs_max=nrhs)
-        p.set_switch(0)
+        p.set_tuning(0, -1, 8, 8)
         plans.append(p)
     return plans
 
@@ -115,7 +118,7 @@ def uneven(fio):
     plans = []
     for sp in specs:
         p = fio.Plan(sp["N"], sp["q"], sp["phase"], sp["params"], "f32", nrhs_max=sp["nrhs"])
-        p.set_switch(0)
+        p.set_tuning(0, -1, 8, 8)
         plans.append(p)
     batch = fio.Batch(plans, [sp["nrhs"] for sp in specs], tune=True)
     xs = [torch.from_numpy(uneven_batch_sources(sp, i)).to(torch.complex64).cuda() for i, sp in enumerate(specs)]
@@ -167,7 +170,8 @@ def test_uneven_batch_dot_test(uneven):
 
 def test_apply_batch_with_one_pointer_per_plan(fio):
     # fio_apply_batch(plans, nplans, f[], u[], nrhs[], stream): each plan's own input and
-    # output pointer; bit-identical to each plan alone (FFMA switch), forward and adjoint,
+    # output pointer; bit-identical to each plan alone (FFMA switch, subtile translations),
+    # forward and adjoint,
     # on repeated calls (the kept batch) and after a plan of the list is destroyed and the
     # list rebuilt (the kept batch is dropped with it)
     plans = _plans(fio, SMALL)
@@ -183,7 +187,7 @@ def test_apply_batch_with_one_pointer_per_plan(fio):
         plans[1].close()
         N, q, phase, nrhs = SMALL[1]
         plans[1] = fio.Plan(N, q, phase, PARAMS[phase], "f32", nrhs_max=nrhs)
-        plans[1].set_switch(0)
+        plans[1].set_tuning(0, -1, 8, 8)
         xs = _sources(SMALL, 7)
         ys = fio.apply_batch(plans, xs)
         torch.cuda.synchronize()
