@@ -302,7 +302,8 @@ int fio_profile_read(fio_plan_t plan, fio_kernel_time_t *out, int max, int *n);
  * kinds 3..8: the tensor-core rate (flop/s, 2 per multiply-add) of tcgen05.mma, M = 128,
  * one CTA per SM issuing back to back with the operands rotating over 16 K-steps:
  * A in tensor memory: 3 TF32 N = 64, 4 BF16 N = 64, 5 TF32 N = 256, 6 BF16 N = 256;
- * A in shared memory: 7 TF32 N = 64, 8 BF16 N = 64.
+ * A in shared memory: 7 TF32 N = 64, 8 BF16 N = 64; A in tensor memory with the MMAs taking
+ * 3 (kind 9) or 2 (kind 10) accumulators in turn: TF32 N = 64.
  * The paper has no counterpart: it is a measurement aid for the roofline. */
 int fio_peak_probe(int kind, double *per_second);
 

@@ -50,7 +50,7 @@ __global__ void k_sfu(float *sink, float a) {
 // bounded wait.  The CTA takes all 512 tensor-memory columns.
 constexpr int kMmaIters = 4096;
 constexpr int kMmaKs = 16;  // K-steps the operands rotate over
-template <bool BF16, int N, bool ASMEM>
+template <bool BF16, int N, bool ASMEM, int NACC = 1>
 __global__ void __launch_bounds__(128, 1) k_mma_probe(int *status) {
   extern __shared__ __align__(128) unsigned char smp[];
   __shared__ uint64_t mbar;
@@ -90,27 +90,28 @@ __global__ void __launch_bounds__(128, 1) k_mma_probe(int *status) {
                                 : tf32_idesc<N>();
     for (int it = 0; it < kMmaIters; it++) {
       const int ks = it % kMmaKs;
-      const uint32_t acc = it > 0 ? 1u : 0u;
+      const uint32_t acc = it >= NACC ? 1u : 0u;
+      const uint32_t dcol = tmem + (uint32_t)(N * (it % NACC));  // NACC accumulators in turn
       const uint64_t db = tc_desc(bb + ks * N * 32, 128, 256);
       if (ASMEM) {
         const uint64_t da = tc_desc(ab + ks * 128 * 32, 128, 256);
         if (BF16)
           asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
                        "l"(da), "l"(db), "r"(idesc), "r"(acc));
         else
           asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
                        "l"(da), "l"(db), "r"(idesc), "r"(acc));
       } else {
         const uint32_t ta = tmem + acol + 8 * ks;
         if (BF16)
           asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                       "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+                       "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dcol),
                        "r"(ta), "l"(db), "r"(idesc), "r"(acc));
         else
           asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                       "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+                       "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dcol),
                        "r"(ta), "l"(db), "r"(idesc), "r"(acc));
       }
     }
@@ -145,6 +146,8 @@ int mma_probe(int kind, double *per_second) {
     if (kind == 6) k_mma_probe<true, 256, false><<<sms, 128, smem>>>(status);
     if (kind == 7) k_mma_probe<false, 64, true><<<sms, 128, smem>>>(status);
     if (kind == 8) k_mma_probe<true, 64, true><<<sms, 128, smem>>>(status);
+    if (kind == 9) k_mma_probe<false, 64, false, 3><<<sms, 128, smem>>>(status);
+    if (kind == 10) k_mma_probe<false, 64, false, 2><<<sms, 128, smem>>>(status);
   };
   cudaFuncSetAttribute(k_mma_probe<false, 64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_mma_probe<true, 64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -152,6 +155,8 @@ int mma_probe(int kind, double *per_second) {
   cudaFuncSetAttribute(k_mma_probe<true, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_mma_probe<false, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_mma_probe<true, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_mma_probe<false, 64, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_mma_probe<false, 64, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -181,7 +186,7 @@ int mma_probe(int kind, double *per_second) {
 }  // namespace
 
 extern "C" int fio_peak_probe(int kind, double *per_second) {
-  if (!per_second || kind < 0 || kind > 8) return FIO_EINVAL;
+  if (!per_second || kind < 0 || kind > 10) return FIO_EINVAL;
   if (kind >= 3) return mma_probe(kind, per_second);
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FIO_EDEVICE;

@@ -472,7 +472,8 @@ def peak_probe(kind: str) -> float:
     """fio_peak_probe on the current device: 'fp32' / 'fp64' flop/s or 'sfu' sin/s."""
     v = ctypes.c_double()
     kinds = {"fp32": 0, "fp64": 1, "sfu": 2, "mma_tf32_n64": 3, "mma_bf16_n64": 4, "mma_tf32_n256": 5,
-             "mma_bf16_n256": 6, "mma_tf32_n64_smem_a": 7, "mma_bf16_n64_smem_a": 8}
+             "mma_bf16_n256": 6, "mma_tf32_n64_smem_a": 7, "mma_bf16_n64_smem_a": 8,
+             "mma_tf32_n64_3acc": 9, "mma_tf32_n64_2acc": 10}
     _check(lib().fio_peak_probe(kinds[kind], ctypes.byref(v)))
     return float(v.value)
 
