@@ -148,7 +148,7 @@ def kernel_flops_bytes(kind: str, info, nrhs: int) -> tuple[float, float]:
 
 
 def _tensor_switch(kind: str, switch_impl: int) -> bool:
-    return kind.startswith("switch") and switch_impl in (1, 3, 4)
+    return kind.startswith("switch") and switch_impl in (1, 3, 4, 5, 6)
 
 
 def kernel_report(prof: dict, info, steps: int, switch_impl: int, tf32_peak=None) -> tuple[dict, dict]:
@@ -504,7 +504,8 @@ def run_ours(args, rank, world, dist):
         "clocks": clk.summary(),
         "cpu_baseline": base,
         "switch_kernel": ["fp32_fma", "tcgen05_tf32_smem_a", "fp32_fma_warp_specialised",
-                          "tcgen05_tf32_tmem_a", "tcgen05_tf32_tmem_a_wide_n"][switch_impl] + " (plan autotuner)",
+                          "tcgen05_tf32_tmem_a", "tcgen05_tf32_tmem_a_wide_n", "tcgen05_tf32x3_tmem_a",
+                          "tcgen05_tf32x3_tmem_a_wide_n"][switch_impl] + " (plan autotuner)",
         "translation_rhs_subtile": trans_rs, "switch_rhs_tile": sw_tile,
         "peak_probes": probes,
         "uneven_batch": ub,

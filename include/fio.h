@@ -148,7 +148,9 @@ typedef struct {
                               warp-specialised and persistent, 3 = tensor cores with the
                               kernel matrix in tensor memory (persistent, one CTA per SM),
                               4 = as 3 with the split-TF32 products as two wide MMAs per
-                              K-step (N = 192 and N = 128) */
+                              K-step (N = 192 and N = 128), 5 and 6 = as 3 and 4 with three
+                              split-TF32 products (A0 B0 + A0 B1 + A1 B0, each entry within
+                              ~3 * 2^-22 of |A||B|) instead of five */
   int trans_rs;            /* FIO_F32, translations of the p-shape (recursion in p, eq. alg2b, and
                               the adjoint of the recursion in x): right-hand sides per subtile
                               (2, 4 or 8), or 32 for the register-tiled kernel (one RHS per lane,
@@ -169,7 +171,7 @@ int fio_plan_info(fio_plan_t plan, fio_plan_info_t *info);
 int fio_check(fio_plan_t plan, void *stream);
 
 /* fio_plan_set_wait_limit -- for tests of the failure path: the limit, in ns, of the
- * waits by which the tensor-memory switch kernels (switch_impl 3, 4) hand chunks between
+ * waits by which the tensor-memory switch kernels (switch_impl 3-6) hand chunks between
  * its producer warps and its MMA warp (0 restores the normal 2 s).  A tiny limit makes
  * those waits expire: the kernel then records the expiry, stops issuing work, still waits
  * with the normal limit for the tensor-core operations it issued, frees its tensor memory
@@ -180,7 +182,7 @@ int fio_plan_set_wait_limit(fio_plan_t plan, unsigned long long ns);
 /* fio_plan_set_switch -- override the autotuner's choice of the FIO_F32 switch
  * kernel: impl 0 = FP32 FMA, 1 = tensor cores (kernel matrix in shared memory),
  * 2 = warp-specialised FP32 FMA, 3 = tensor cores (kernel matrix in tensor memory), 4 = as 3
- * with two wide MMAs per K-step.
+ * with two wide MMAs per K-step, 5 and 6 = as 3 and 4 with three split-TF32 products.
  * FIO_EINVAL if the plan is FIO_F64 or the kernel does not fit this plan (its
  * shared memory need: 1 and 2 are not available for every q). */
 int fio_plan_set_switch(fio_plan_t plan, int impl);

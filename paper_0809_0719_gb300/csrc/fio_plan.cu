@@ -564,7 +564,7 @@ int fio_check(fio_plan_t p, void *stream) {
 
 int fio_plan_set_switch(fio_plan_t p, int impl) {
   if (!p) return fail(FIO_EINVAL, "plan is NULL");
-  if (impl < 0 || impl > 4) return fail(FIO_EINVAL, "switch impl %d must be 0 .. 4", impl);
+  if (impl < 0 || impl > 6) return fail(FIO_EINVAL, "switch impl %d must be 0 .. 6", impl);
   if (p->d.precision != FIO_F32) return fail(FIO_EINVAL, "only FIO_F32 plans have a choice of switch kernel");
   int avail = 0;
   dispatch(p->d, fio::RUN_TC_OK, nullptr, nullptr, 1, nullptr, -1, &avail);

@@ -38,7 +38,8 @@ struct PlanDev {
   int smem_optin;
   int num_sms;
   int switch_impl;  // FP32 switch: 0 FFMA, 1 tensor cores (A in smem), 2 warp-specialised FFMA,
-                    // 3 tensor cores (A in tensor memory), 4 as 3 with two wide MMAs per K-step;
+                    // 3 tensor cores (A in tensor memory), 4 as 3 with two wide MMAs per K-step,
+                    // 5 and 6 as 3 and 4 with 3 split-TF32 products instead of 5;
                     // chosen by the plan's autotuner
   int trans_rs;     // FP32 translations of the p-shape (recursion in p, adjoint of the recursion
                     // in x): RHS per subtile 2, 4 or 8, or 32 for the register-tiled kernels
@@ -191,6 +192,12 @@ template <typename R, int Q> struct Runner {
     return check();
   }
 
+  static size_t tm_smem(int v) {
+    return v == 0 ? TmShape<Q, false, 5>::smem_bytes()
+         : v == 1 ? TmShape<Q, true, 5>::smem_bytes()
+         : v == 2 ? TmShape<Q, false, 3>::smem_bytes()
+                  : TmShape<Q, true, 3>::smem_bytes();
+  }
   template <bool FWD> int sw(const CT *in, CT *out) {
     if constexpr (sizeof(R) == 4) {
       if (fast32() && p.switch_impl == 2 && SwWs<Q>::smem <= p.smem_optin) {
@@ -205,16 +212,20 @@ template <typename R, int Q> struct Runner {
         k<<<grid, SwWs<Q>::threads, SwWs<Q>::smem, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, nwork);
         return check();
       }
-      const bool wide = p.switch_impl == 4;
-      const size_t smem_tm = wide ? TmShape<Q, true>::smem_bytes() : TmShape<Q>::smem_bytes();
-      if (fast32() && (p.switch_impl == 3 || wide) && p.status && smem_tm <= (size_t)p.smem_optin) {
+      // 3 / 4: narrow / wide MMAs with 5 split-TF32 products; 5 / 6: the same with 3
+      const int tmv = p.switch_impl - 3;
+      const size_t smem_tm = tm_smem(tmv);
+      if (fast32() && tmv >= 0 && tmv < 4 && p.status && smem_tm <= (size_t)p.smem_optin) {
         const long long pairs = (1LL << (2 * p.lm)) * nb_at(p.L - p.lm);
         const Geom g = geom(p.lm, kRMax, 1, pairs);
         const long long nsu = pairs >> (p.L - p.lm);  // (box A, angular box) super-units
         dim3 grid((unsigned)std::min<long long>(nsu, std::max(1, p.num_sms)), (unsigned)((nrhs + kRMax - 1) / kRMax));
         if (count_only) return check();
         pre(FWD ? K_SWITCH : K_SWITCH_ADJ);
-        auto k = wide ? k32_switch_tm<Q, FWD, true> : k32_switch_tm<Q, FWD, false>;
+        auto k = tmv == 0 ? k32_switch_tm<Q, FWD, false, 5>
+                 : tmv == 1 ? k32_switch_tm<Q, FWD, true, 5>
+                 : tmv == 2 ? k32_switch_tm<Q, FWD, false, 3>
+                            : k32_switch_tm<Q, FWD, true, 3>;
         set_smem(k, p.smem_optin);
         k<<<grid, kTmThreads, smem_tm, st>>>(p.tb, p.tf, p.ph, g, (const float2 *)in, (float2 *)out, p.status,
                                              p.handoff_ns);
@@ -397,12 +408,12 @@ template <typename R, int Q> struct Runner {
   }
 
   // Autotuner: time the alternatives on the plan's state buffers (their contents do
-  // not matter) and keep the faster: the FFMA vs the tensor-core switch, and 4- vs
-  // 8-RHS translation subtiles (at the plan's first translation level).  Returns the
-  // chosen switch implementation (0 or 1).
+  // not matter) and keep the fastest: the switch implementations of switch_impls(), and
+  // the RHS subtile width or register-tiled kernels of each translation shape.  Returns
+  // the chosen switch implementation.
   // Bit i set: switch implementation i can run this plan (0 FFMA, 1 tensor cores with
-  // the kernel matrix in shared memory, 2 warp-specialised FFMA, 3 tensor cores with
-  // the kernel matrix in tensor memory).
+  // the kernel matrix in shared memory, 2 warp-specialised FFMA, 3-6 tensor cores with
+  // the kernel matrix in tensor memory: narrow or wide MMAs, 5 or 3 products).
   int switch_impls() const {
     if constexpr (sizeof(R) != 4) {
       return 1;
@@ -411,9 +422,8 @@ template <typename R, int Q> struct Runner {
       int m = 1;
       if (p.status && TcShape<Q>::smem_bytes() <= (size_t)p.smem_optin) m |= 2;
       if (SwWs<Q>::smem <= p.smem_optin) m |= 4;
-      if (p.status && TmShape<Q>::smem_bytes() <= (size_t)p.smem_optin && (1 << (p.L - p.lm)) <= kTmNb1Max) m |= 8;
-      if (p.status && TmShape<Q, true>::smem_bytes() <= (size_t)p.smem_optin && (1 << (p.L - p.lm)) <= kTmNb1Max)
-        m |= 16;
+      for (int v = 0; v < 4; v++)
+        if (p.status && tm_smem(v) <= (size_t)p.smem_optin && (1 << (p.L - p.lm)) <= kTmNb1Max) m |= 8 << v;
       return m;
     }
   }
@@ -471,7 +481,7 @@ template <typename R, int Q> struct Runner {
       const int avail = switch_impls();
       float best = 1e30f;
       int pick = 0, pick_rb = 4;
-      for (int impl = 0; impl < 5; impl++) {
+      for (int impl = 0; impl < 7; impl++) {
         if (!(avail >> impl & 1)) continue;
         for (int rb : {4, 8}) {
           if (impl != 0 && rb != 4) continue;  // only the one-pair-per-CTA kernel has both tiles

@@ -381,14 +381,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k32_switch_tc(Tables tb, Tables
 // Second tensor-core switch: the kernel matrix lives in tensor memory.
 //
 // Same real GEMM as above (A = kernel, M = q^2 rows padded to 128; B = the
-// coefficients in the [Re, Im; -Im, Re] form, N = 64; split TF32, 5 products),
+// coefficients in the [Re, Im; -Im, Re] form, N = 64; split TF32, 5 or 3 products),
 // but A never touches shared memory: the producer thread that owns row t of A
 // (TMEM lane t) computes its kernel entries and writes both TF32 parts to tensor
 // memory with tcgen05.st, and the MMA reads A from there (the [a-tmem] operand
 // form), so only B (2 KB per MMA) is read from shared memory.
 //
 // K is cut into chunks of kTmCK MMA K-steps.  A chunk occupies one A slot in
-// tensor memory (2 parts x kTmKC columns) and one B slot in shared memory (3
+// tensor memory (2 parts x kTmKC columns) and one B slot in shared memory (3 or 2
 // parts); kTmNB slots of each form a ring, so the producers run up to kTmNB
 // chunks ahead of the MMA warp.  Tensor memory (512 columns, one CTA per SM):
 // two 64-column accumulators (the epilogue of a pair overlaps the MMAs of the
@@ -405,7 +405,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k32_switch_tc(Tables tb, Tables
 //   fre[j]    MMA -> producers   (tcgen05.commit)            slot j read
 //   dfull[d]  MMA -> producers   (tcgen05.commit)            accumulator d complete
 //   dempty[d] producers -> MMA   (arrive count kTmProducers) accumulator d read out
-//   tab[b]    producers          (arrive count kTmProducers) tables + inputs of a pair ready
+// On the producer side one warp (kTmWaiter) polls fre / dfull and the other producer warps
+// park at named barrier 1 (bar.red.and: every producer gets the same go/abort outcome),
+// so only one warp spends issue slots on a hand-off; the producers' own step (tables and
+// inputs of the next pair in place) is that barrier alone.
 // ---------------------------------------------------------------------------
 constexpr int kTmProducers = 512;               // 16 producer warps, 4 per TMEM lane quarter
 constexpr int kTmThreads = kTmProducers + 32;   // + 1 MMA warp
@@ -417,34 +420,44 @@ constexpr int kTmAcols = 2 * kTmKC;             // TMEM columns of one A slot (t
 constexpr int kTmSmemFloor = 120 * 1024;        // > half an SM's shared memory: one CTA (512 TMEM columns) per SM
 constexpr int kTmNb1Max = 64;                   // radial boxes at the switch level (2^ceil(L/2), N <= 4096)
 constexpr int kTmPQ = kTmProducers / 128;        // producer warps per lane quarter
+constexpr int kTmWaiter = kTmProducers / 32 - 1; // the producer warp that polls the MMA warp's mbarriers
 static_assert(kTmProducers % 128 == 0, "producer warps per lane quarter");
 
-// W (wide): the split-TF32 products as two wide MMAs per K-step, A0 x [B0|B1|B2] (N = 192)
-// and A1 x [B0|B1] (N = 128), into two double-buffered 192-column accumulators whose three
-// 64-column blocks the epilogue sums; tensor memory then holds two A slots of 4 K-steps.
-template <bool W> struct TmCfg {
-  static constexpr int CK = W ? 4 : kTmCK;         // MMA K-steps per chunk
+// NP: split-TF32 products per K-step.  5: A = A0 + A1, B = B0 + B1 + B2 (B2 the exact FP32
+// remainder), A0 B0 + A0 B1 + A1 B0 + A0 B2 + A1 B1; the dropped terms are ~2^-22 |A||B|
+// and the truncation of B2 ~2^-33 |B|.  3: B = B0 + B1 as well, A0 B0 + A0 B1 + A1 B0;
+// A1 B1 and the two split residuals each stay below 2^-22 |A||B| (|A1| <= 2^-11 |A|,
+// |A - A0 - A1| <= 2^-22 |A|, likewise for B), so a product is off by at most ~3 * 2^-22
+// of |A||B|: about the rounding an FP32 sum of the q^2-term row already carries.
+// W (wide): the products as two wide MMAs per K-step into one accumulator whose 64-column
+// blocks the epilogue sums: A0 x [B0|B1|B2] (N = 192) and A1 x [B0|B1] (N = 128) for NP = 5;
+// A0 x [B0|B1] (N = 128) and A1 x B0 (N = 64) for NP = 3.  Two accumulators double-buffer
+// the pairs.
+template <bool W, int NP = 5> struct TmCfg {
+  static_assert(NP == 5 || NP == 3, "split-TF32 products per K-step");
+  static constexpr int PB = NP == 5 ? 3 : 2;       // TF32 parts of B
+  static constexpr int CK = (W && NP == 5) ? 4 : kTmCK;  // MMA K-steps per chunk
   static constexpr int KC = 8 * CK;                // K columns per chunk
   static constexpr int NB = W ? 2 : kTmNB;         // ring slots
-  static constexpr int ACC = W ? 192 : 64;         // columns of one accumulator
+  static constexpr int ACC = W ? 64 * PB : 64;     // columns of one accumulator
   static constexpr int DC = 2 * ACC;               // both accumulators
   static constexpr int AC = 2 * KC;                // one A slot (two TF32 parts)
   static_assert(DC + NB * AC <= 512, "tensor memory budget");
   static_assert((KC / 2) % kTmPQ == 0, "producer warps split a chunk's columns evenly");
 };
 
-template <int Q, bool W = false> struct TmShape {
-  typedef TmCfg<W> C;
+template <int Q, bool W = false, int NP = 5> struct TmShape {
+  typedef TmCfg<W, NP> C;
   static constexpr int Q2 = Q * Q;
   static constexpr int KP = ((2 * Q2 + 7) / 8) * 8;        // padded K
   static constexpr int KS = KP / 8;                        // MMA K-steps per pair
   static constexpr int NCH = (KS + C::CK - 1) / C::CK;     // chunks per pair (the last may be partial)
   static constexpr int B_FLOATS = 64 * C::KC;              // one TF32 part of one B slot
-  static constexpr size_t b_bytes = (size_t)C::NB * kTcPB * B_FLOATS * 4;
+  static constexpr size_t b_bytes = (size_t)C::NB * C::PB * B_FLOATS * 4;
   static constexpr size_t in_bytes = (size_t)2 * kRMax * Q2 * 8;
   static constexpr size_t gt_bytes = (size_t)2 * Q2 * Q * sizeof(df);
   static constexpr size_t rho_bytes = (size_t)kTmNb1Max * Q * sizeof(df);
-  static constexpr int nbar = 2 * C::NB + 7;
+  static constexpr int nbar = 2 * C::NB + 5;
   static constexpr size_t used = b_bytes + in_bytes + gt_bytes + rho_bytes + nbar * 8 + 16;
   static constexpr size_t smem_bytes() { return used > (size_t)kTmSmemFloor ? used : (size_t)kTmSmemFloor; }
 };
@@ -506,14 +519,14 @@ __device__ __forceinline__ void tm_arrive(uint64_t *mbar) { mbar_arrive(mbar); }
 // handoff_ns: limit of the waits between the producer warps and the MMA warp (0: the
 // normal 2 s); a test sets it tiny to make them expire.  The final drain of the issued
 // MMAs (fin) always waits with the normal limit.
-template <int Q, bool FWD, bool W = false>
+template <int Q, bool FWD, bool W = false, int NP = 5>
 __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, TablesF tf, Phase ph, Geom g,
                                                                 const float2 *__restrict__ in,
                                                                 float2 *__restrict__ out, int *status,
                                                                 unsigned long long handoff_ns) {
-  typedef TmShape<Q, W> S;
-  typedef TmCfg<W> C;
-  constexpr int Q2 = S::Q2, KS = S::KS, NCH = S::NCH;
+  typedef TmShape<Q, W, NP> S;
+  typedef TmCfg<W, NP> C;
+  constexpr int Q2 = S::Q2, KS = S::KS, NCH = S::NCH, PB = C::PB;
   constexpr int CPW = C::KC / 2 / kTmPQ;  // complex kernel columns per producer warp and chunk
   constexpr int RPW = kRMax / kTmPQ;      // RHS per producer warp in the epilogue
   constexpr int KCC = C::KC / 4;  // core-matrix columns (4 K each) per chunk
@@ -526,8 +539,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
   uint64_t *fre = full + C::NB;
   uint64_t *dfull = fre + C::NB;
   uint64_t *dempty = dfull + 2;
-  uint64_t *tab = dempty + 2;
-  uint64_t *fin = tab + 2;
+  uint64_t *fin = dempty + 2;
   uint32_t *tmem_s = (uint32_t *)(fin + 1);
   volatile int *abort_s = (volatile int *)(tmem_s + 1);
 
@@ -552,7 +564,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
 
   if (tid == 0) {
     for (int b = 0; b < S::nbar; b++) {
-      const int cnt = (b < C::NB || (b >= 2 * C::NB + 2 && b < 2 * C::NB + 6)) ? kTmProducers : 1;
+      const int cnt = (b < C::NB || (b >= 2 * C::NB + 2 && b < 2 * C::NB + 4)) ? kTmProducers : 1;
       const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&full[b]);
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(cnt));
     }
@@ -579,6 +591,17 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
     }
     return ok;
   };
+  // producers only: AND of `ok` over all producer threads at named barrier 1
+  auto psync = [&](bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.and.pred po, 1, %2, pi;\nselp.u32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "n"(kTmProducers)
+        : "memory");
+    return r != 0;
+  };
+  auto pwait = [&](uint64_t *mb, uint32_t parity) { return psync(warp == kTmWaiter ? waitw(mb, parity) : true); };
 
   if (warp == kTmProducers / 32) {
     // ------------------------------------------------------------ MMA warp
@@ -599,20 +622,23 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
           const int nks = min(C::CK, KS - c * C::CK);
           const uint32_t a0 = tmem + C::DC + j * C::AC;
           for (int ks = 0; ks < nks; ks++) {
-            uint64_t dB[kTcPB];
+            uint64_t dB[PB];
 #pragma unroll
-            for (int q_ = 0; q_ < kTcPB; q_++)
-              dB[q_] = tc_desc(aB + ((j * kTcPB + q_) * S::B_FLOATS) * 4 + ks * 256, 128, sbo);
+            for (int q_ = 0; q_ < PB; q_++)
+              dB[q_] = tc_desc(aB + ((j * PB + q_) * S::B_FLOATS) * 4 + ks * 256, 128, sbo);
             const uint32_t ta0 = a0 + 8 * ks, ta1 = a0 + C::KC + 8 * ks;
-            if (W) {  // the B parts lie one after another: one descriptor spans 192 or 128 rows
-              tm_mma_n<192>(dtm, ta0, dB[0], (c > 0 || ks > 0) ? 1u : 0u);
-              tm_mma_n<128>(dtm, ta1, dB[0], 1u);
+            const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+            if (W) {  // the B parts lie one after another: one descriptor spans 64 PB rows
+              tm_mma_n<64 * PB>(dtm, ta0, dB[0], acc);
+              tm_mma_n<64 * (PB - 1)>(dtm, ta1, dB[0], 1u);
             } else {
-              tm_mma(dtm, ta0, dB[0], (c > 0 || ks > 0) ? 1u : 0u);
+              tm_mma(dtm, ta0, dB[0], acc);
               tm_mma(dtm, ta0, dB[1], 1u);
               tm_mma(dtm, ta1, dB[0], 1u);
-              tm_mma(dtm, ta0, dB[2], 1u);
-              tm_mma(dtm, ta1, dB[1], 1u);
+              if (NP == 5) {
+                tm_mma(dtm, ta0, dB[PB - 1], 1u);
+                tm_mma(dtm, ta1, dB[1], 1u);
+              }
             }
           }
           tc_commit(&fre[j]);
@@ -665,10 +691,10 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
         gtb[idx] = g_eval(tf.ph, xdt, p2f(tb, tf, lb, b2, s2, Q));
       }
     };
-    // phase parities: use k of tab[b] / dfull[d] (buffers alternate) belongs to pair 2k + index
+    // phase parities: use k of dfull[d] (accumulators alternate) belongs to pair 2k + d
     auto epilogue = [&](long long k) {
       const int d = (int)(k & 1);
-      if (!waitw(&dfull[d], (uint32_t)(k >> 1) & 1)) return false;
+      if (!pwait(&dfull[d], (uint32_t)(k >> 1) & 1)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (arows) {
         static_assert(RPW == 8, "epilogue reads 8 columns per warp");
@@ -676,9 +702,9 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
         float re[RPW], im[RPW];
         tc_ld8(trow, re);
         tc_ld8(trow + 32, im);
-        if (W) {  // the A0 B1 + A1 B1 and A0 B2 blocks of the wide accumulator, added in order
+        if (W) {  // the further 64-column blocks of the wide accumulator, added in order
 #pragma unroll
-          for (int blk = 1; blk < 3; blk++) {
+          for (int blk = 1; blk < PB; blk++) {
             float re2[RPW], im2[RPW];
             tc_ld8(trow + 64 * blk, re2);
             tc_ld8(trow + 64 * blk + 32, im2);
@@ -707,14 +733,13 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
       prefetch(0, 0);
       tables(0, 0);
       cp_async_wait(0);
-      tm_arrive(&tab[0]);
     }
     uint32_t gc = 0;
     long long k = 0;
     bool live = true;
     for (; su_of(k) < nsu && live; k++) {
       const int b = (int)(k & 1);
-      if (!waitw(&tab[b], (uint32_t)(k >> 1) & 1)) break;
+      if (!psync(!*abort_s)) break;  // inputs and tables of pair k in place
       prefetch(k + 1, b ^ 1);
       const float2 *ins = instage + b * kRMax * Q2;
       const df *gtb = gt + (int)((k >> lb) & 1) * Q2 * Q;
@@ -733,7 +758,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
       const df *grow = FWD ? gtb + oc * Q : gtb + oc % Q;
       for (int c = 0; c < NCH; c++, gc++) {
         const int j = (int)(gc % C::NB);
-        if (gc >= C::NB && !waitw(&fre[j], (gc / C::NB - 1) & 1)) { live = false; break; }
+        if (gc >= C::NB && !pwait(&fre[j], (gc / C::NB - 1) & 1)) { live = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // A: this lane's row, CPW complex columns, both TF32 parts, into tensor memory.  The
         // fast path is branch-free (indices clamped, invalid entries selected to zero) so the
@@ -787,22 +812,22 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
         // B: lane r builds rows r and 32 + r of core-matrix column kc from X[r][s0], X[r][s0+1]
         // (s0 = the chunk's first complex column + 2 kc): [Re, -Im] and [Im, Re], three TF32 parts
         if (bidx >= 0) {
-          float *cb = bs + j * kTcPB * S::B_FLOATS;
+          float *cb = bs + j * PB * S::B_FLOATS;
           for (int kc = bidx; kc < KCC; kc += bstride) {
             const int s0 = c * (C::KC / 2) + 2 * kc;
             const int rr = lane < rc ? lane : 0;
             float2 x0 = ins[rr * Q2 + min(s0, Q2 - 1)], x1 = ins[rr * Q2 + min(s0 + 1, Q2 - 1)];
             if (!(lane < rc && s0 < Q2)) x0 = make_float2(0.f, 0.f);  // rows beyond rc were not loaded
             if (!(lane < rc && s0 + 1 < Q2)) x1 = make_float2(0.f, 0.f);
-            float ar[kTcPB], ai[kTcPB], br[kTcPB], bi[kTcPB];
-            tf32_split<kTcPB>(x0.x, ar);
-            tf32_split<kTcPB>(x0.y, ai);
-            tf32_split<kTcPB>(x1.x, br);
-            tf32_split<kTcPB>(x1.y, bi);
+            float ar[PB], ai[PB], br[PB], bi[PB];
+            tf32_split<PB>(x0.x, ar);
+            tf32_split<PB>(x0.y, ai);
+            tf32_split<PB>(x1.x, br);
+            tf32_split<PB>(x1.y, bi);
             float *top = cb + ((lane >> 3) * KCC + kc) * 32 + (lane & 7) * 4;
             float *bot = top + 4 * KCC * 32;
 #pragma unroll
-            for (int q_ = 0; q_ < kTcPB; q_++) {
+            for (int q_ = 0; q_ < PB; q_++) {
               *reinterpret_cast<float4 *>(top + q_ * S::B_FLOATS) = make_float4(ar[q_], -ai[q_], br[q_], -bi[q_]);
               *reinterpret_cast<float4 *>(bot + q_ * S::B_FLOATS) = make_float4(ai[q_], ar[q_], bi[q_], br[q_]);
             }
@@ -817,10 +842,9 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
       if (su_of(k + 1) < nsu) {
         if (((k + 1) & (nb1 - 1)) == 0) tables(k + 1, (int)(((k + 1) >> lb) & 1));
         cp_async_wait(0);
-        tm_arrive(&tab[b ^ 1]);
       }
     }
-    if (live && !*abort_s && k > 0) epilogue(k - 1);
+    if (live && k > 0 && psync(!*abort_s)) epilogue(k - 1);
     cp_async_wait(0);
   }
   // the MMA warp has drained its MMAs (fin) and the producers their loads

@@ -225,7 +225,7 @@ class Plan:
         """fio_plan_set_switch: 0 = FP32 FMA switch kernel, 1 = tensor-core switch kernel
         (kernel matrix in shared memory), 2 = warp-specialised persistent FP32 FMA switch
         kernel, 3 = tensor-core switch kernel with the kernel matrix in tensor memory, 4 = as 3 with
-        two wide MMAs per K-step."""
+        two wide MMAs per K-step, 5 and 6 = as 3 and 4 with three split-TF32 products instead of five."""
         _check(lib().fio_plan_set_switch(self._h, int(impl)))
         self.info.switch_impl = int(impl)
 

@@ -1,8 +1,9 @@
 """GPU parity at the workloads' full sizes, against the FP64 CPU oracle.
 
 * N = 1024, q = 9, ellipse [2, 1, 16, 1], 32 complex64 RHS (seeds 0..31), s = 3, e = 2,
-  FP32 form with the tensor-memory tcgen05 switch forced: the launch configuration the
-  benchmark times.  Only this size takes state offsets beyond 2^31 elements (87 GB per
+  FP32 form with each tensor-memory tcgen05 switch forced in turn (5 or 3 split-TF32
+  products, narrow or wide MMAs; the plan's autotuner picks among them): the launch
+  configurations the benchmark times.  Only this size takes state offsets beyond 2^31 elements (87 GB per
   level), 32 radial boxes at the switch level and thousands of pairs per persistent CTA.
   The oracle cannot run the butterfly at this size, so every RHS is compared on 512 seeded
   x with the oracle's direct sum of eq. dfio (eq. err), and the FP64 form on RHS 0 and 31
@@ -54,30 +55,34 @@ def test_headline_every_rhs_against_direct_sum(fio, oracle):
     # the oracle's sums of the values the FP32 form sees (complex64 inputs, widened exactly)
     ref = oracle.direct_multi(N, oracle.ELLIPSE, list(ELL16), F32.astype(np.complex128), xi)
 
+    G = gaussian_batch(N, range(100, 100 + R)).astype(np.complex64)
+    ki = sample_indices(N, 128, 1001)
+    # the adjoint against the oracle's adjoint direct sum at 128 seeded frequencies (RHS 0)
+    fref = oracle.direct_adjoint(N, oracle.ELLIPSE, list(ELL16), G[0].astype(np.complex128), ki)
+    res = {}
     plan = fio.Plan(N, q, "ellipse", ELL16, "f32", nrhs_max=R, s=3, e=2)
     try:
-        plan.set_switch(3)
         assert plan.info.pairs_per_level * R * q * q > 2 ** 31  # state offsets beyond 32 bits
         f = torch.from_numpy(F32).cuda()
-        u = plan.apply(f)
+        g = torch.from_numpy(G).cuda()
         xt = torch.from_numpy(xi).cuda()
-        U = u.reshape(R, -1)[:, xt].cpu().numpy()
-        # dot test at this size: <g, B f> against <B^H g, f> over the 32 RHS
-        g = torch.from_numpy(gaussian_batch(N, range(100, 100 + R)).astype(np.complex64)).cuda()
-        fb = plan.adjoint(g)
-        plan.check()  # no bounded wait of the tensor-core switch expired
-        a = torch.vdot(g.to(torch.complex128).flatten(), u.to(torch.complex128).flatten())
-        b = torch.vdot(fb.to(torch.complex128).flatten(), f.to(torch.complex128).flatten())
-        dot = abs(a - b).item() / abs(a).item()
-        # the adjoint against the oracle's adjoint direct sum at 128 seeded frequencies (RHS 0)
-        ki = sample_indices(N, 128, 1001)
-        fref = oracle.direct_adjoint(N, oracle.ELLIPSE, list(ELL16), g[0].cpu().numpy().astype(np.complex128), ki)
-        err_adj = rel(fb[0].reshape(-1)[torch.from_numpy(ki).cuda()].cpu().numpy(), fref)
-        del f, u, g, fb
+        for sw in (3, 4, 5, 6):
+            plan.set_switch(sw)
+            u = plan.apply(f)
+            U = u.reshape(R, -1)[:, xt].cpu().numpy()
+            # dot test at this size: <g, B f> against <B^H g, f> over the 32 RHS
+            fb = plan.adjoint(g)
+            plan.check()  # no bounded wait of the tensor-core switch expired
+            a = torch.vdot(g.to(torch.complex128).flatten(), u.to(torch.complex128).flatten())
+            b = torch.vdot(fb.to(torch.complex128).flatten(), f.to(torch.complex128).flatten())
+            dot = abs(a - b).item() / abs(a).item()
+            err_adj = rel(fb[0].reshape(-1)[torch.from_numpy(ki).cuda()].cpu().numpy(), fref)
+            res[sw] = ([rel(U[r], ref[r]) for r in range(R)], dot, err_adj)
+            del u, fb
+        del f, g
     finally:
         plan.close()
         torch.cuda.empty_cache()
-    err32 = [rel(U[r], ref[r]) for r in range(R)]
 
     plan64 = fio.Plan(N, q, "ellipse", ELL16, "f64", nrhs_max=2, s=3, e=2)
     try:
@@ -89,10 +94,11 @@ def test_headline_every_rhs_against_direct_sum(fio, oracle):
     err64 = [rel(u64[0], ref[0]), rel(u64[1], ref[R - 1])]
     bar = max(2 * max(err64), 1e-5)
     assert max(err64) < 2e-5, err64  # q = 9: the butterfly's own error is ~6e-6
-    assert err32[0] <= max(2 * err64[0], 1e-5) and err32[R - 1] <= max(2 * err64[1], 1e-5), (err32, err64)
-    assert max(err32) <= bar, (max(err32), bar)
-    assert dot < 1e-6, dot
-    assert err_adj < 1e-4, err_adj
+    for sw, (err32, dot, err_adj) in res.items():
+        assert err32[0] <= max(2 * err64[0], 1e-5) and err32[R - 1] <= max(2 * err64[1], 1e-5), (sw, err32, err64)
+        assert max(err32) <= bar, (sw, max(err32), bar)
+        assert dot < 1e-6, (sw, dot)
+        assert err_adj < 1e-4, (sw, err_adj)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])

@@ -81,11 +81,13 @@ CASES = [
 @pytest.mark.parametrize("N,q,phase,s,e", CASES)
 @pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 5, None), ("f32", 3, 0), ("f32", 9, 0),
                                           ("f32", 3, 1), ("f32", 33, 1), ("f32", 3, 2), ("f32", 33, 2),
-                                          ("f32", 3, 3), ("f32", 33, 3), ("f32", 3, 4), ("f32", 33, 4)])
+                                          ("f32", 3, 3), ("f32", 33, 3), ("f32", 3, 4), ("f32", 33, 4),
+                                          ("f32", 3, 5), ("f32", 33, 5), ("f32", 3, 6), ("f32", 33, 6)])
 def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, nrhs, sw):
     # sw: switch kernel of the FP32 form (0 FP32 FMA, 1 tensor cores with the kernel matrix in
-    # shared memory, 2 warp-specialised FP32 FMA, 3 tensor cores with it in tensor memory),
-    # forced past the autotuner
+    # shared memory, 2 warp-specialised FP32 FMA, 3 tensor cores with it in tensor memory, 4 as
+    # 3 with wide MMAs, 5 and 6 as 3 and 4 with three split-TF32 products), forced past the
+    # autotuner
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
     try:
@@ -107,7 +109,8 @@ def test_forward_matches_oracle_butterfly(fio, oracle, N, q, phase, s, e, prec, 
 
 @pytest.mark.parametrize("N,q,phase,s,e", [(64, 5, "ellipse", 0, 2), (128, 7, "circle", 3, 2), (32, 3, "separable", 0, 1)])
 @pytest.mark.parametrize("prec,nrhs,sw", [("f64", 1, None), ("f64", 3, None), ("f32", 10, 0), ("f32", 10, 1),
-                                          ("f32", 10, 2), ("f32", 10, 3), ("f32", 10, 4)])
+                                          ("f32", 10, 2), ("f32", 10, 3), ("f32", 10, 4), ("f32", 10, 5),
+                                          ("f32", 10, 6)])
 def test_adjoint_matches_oracle_adjoint(fio, oracle, N, q, phase, s, e, prec, nrhs, sw):
     pid, prm = PH[phase]
     plan = fio.Plan(N, q, pid, prm, prec, nrhs_max=nrhs, s=s, e=e)
@@ -142,7 +145,7 @@ def test_every_stage_matches_oracle(fio, oracle, N, q, s, e):
 
 
 @pytest.mark.parametrize("prec,tol,sw", [("f64", 1e-12, None), ("f32", 1e-6, 0), ("f32", 1e-6, 1), ("f32", 1e-6, 2),
-                                         ("f32", 1e-6, 3), ("f32", 1e-6, 4)])
+                                         ("f32", 1e-6, 3), ("f32", 1e-6, 4), ("f32", 1e-6, 5), ("f32", 1e-6, 6)])
 @pytest.mark.parametrize("N,q,e", [(64, 5, 2), (256, 9, 2)])
 def test_dot_test(fio, prec, tol, sw, N, q, e):
     plan = fio.Plan(N, q, "ellipse", ELL16, prec, nrhs_max=2, e=e)
@@ -168,7 +171,8 @@ def test_dot_test(fio, prec, tol, sw, N, q, e):
 
 
 @pytest.mark.parametrize("N,q,phase,nrhs", [(64, 9, "ellipse", 33), (128, 5, "circle", 7)])
-@pytest.mark.parametrize("sw,tile,rs", [(0, 4, 2), (0, 8, 4), (0, 8, 8), (2, 4, 8), (3, 4, 4), (4, 4, 32)])
+@pytest.mark.parametrize("sw,tile,rs", [(0, 4, 2), (0, 8, 4), (0, 8, 8), (2, 4, 8), (3, 4, 4), (4, 4, 32), (5, 4, 32),
+                                       (6, 4, 8)])
 def test_every_tuning_choice_matches_oracle(fio, oracle, N, q, phase, nrhs, sw, tile, rs):
     # the autotuner picks among these per plan; each must give the oracle's result
     pid, prm = PH[phase]
@@ -294,12 +298,12 @@ def test_tensor_memory_switch_matches_fma_switch(fio, N, q, nrhs):
     try:
         f = torch.from_numpy(gaussian_batch(N, range(400, 400 + nrhs))).to(plan.dtype).cuda()
         out = {}
-        for sw in (0, 3, 4):
+        for sw in (0, 3, 4, 5, 6):
             plan.set_switch(sw)
             out[sw] = (plan.apply(f).to(torch.complex128), plan.adjoint(f).to(torch.complex128))
             plan.check()
         for k in range(2):
-            for sw in (3, 4):
+            for sw in (3, 4, 5, 6):
                 a, b = out[sw][k], out[0][k]
                 for r in range(nrhs):
                     assert rel(a[r].cpu().numpy(), b[r].cpu().numpy()) < 2e-6, (sw, k, r)
