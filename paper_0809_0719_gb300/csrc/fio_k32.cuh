@@ -198,6 +198,17 @@ __device__ __forceinline__ void store_run(float2 *dst, const float2 *src, int n,
 __device__ __forceinline__ void store_run(float2 *dst, const float2 *src, int n) {
   store_run(dst, src, n, threadIdx.x, blockDim.x);
 }
+// Bulk copy (TMA engine) of `bytes` (a multiple of 16) from shared to global memory, both
+// 16-byte aligned, as part of the calling thread's current bulk group; commit, and wait
+// until the thread's groups have read their shared-memory source (read) or completed.
+__device__ __forceinline__ void bulk_s2g(void *gmem, const void *smem, uint32_t bytes) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gmem), "r"(sa), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait(int pending) {
   if (pending) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
@@ -715,11 +726,16 @@ __global__ void __launch_bounds__(SwWs<Q>::threads, 1) k32_switch_ws(Tables tb, 
 // ---------------------------------------------------------------------------
 // FP32 initialization (eq. alg2a), as k_init with df phases; one CTA per box B and
 // up to 32 RHS; the phases of GA boxes A are staged at a time, then each thread
-// accumulates one (RHS, t1) row for every A of the chunk.
+// accumulates one (RHS, t1) row for every A of the chunk.  With use_stage (shared room
+// for one kRMax q^2 output block after the tables) and a full 32-RHS tile, each block
+// (A, B) goes through shared memory and leaves as one contiguous run: a bulk copy by the
+// TMA engine where the run is 16-byte aligned (an even RHS count), else 16-byte stores.
+// Otherwise each thread stores its row directly (9 values at a 72-byte stride per lane).
 // ---------------------------------------------------------------------------
 template <int Q>
 __device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &tf, const Phase &ph, const Geom &g, int maxsrc, int GA,
-                                              const float2 *__restrict__ f, float2 *__restrict__ st, long long bx_, int by_) {
+                                              const float2 *__restrict__ f, float2 *__restrict__ st, long long bx_, int by_,
+                                              bool use_stage = false) {
   constexpr int Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l0 = g.l, lb = g.L - g.l, e = g.e;
@@ -734,6 +750,9 @@ __device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &t
   float2 *pk = fv + maxsrc * kRMax;    // [GA][maxsrc]
   float2 *post = pk + GA * maxsrc;     // [GA][Q2]
   float *w = (float *)(post + GA * Q2);  // [maxsrc][2Q]
+  float2 *stage = (float2 *)(((uintptr_t)(w + maxsrc * 2 * Q) + 15) & ~(uintptr_t)15);  // [kRMax][Q2]
+  const bool staged = use_stage && rt == kRMax && (int)blockDim.x == kRMax * Q;
+  const bool bulk = staged && ((g.nrhs * Q2) & 1) == 0;
   for (int idx = threadIdx.x; idx < ns * rt; idx += blockDim.x) {
     const int j = idx / rt, r = idx % rt;
     fv[j * kRMax + r] = f[(long long)(r0 + r) * NN + tb.src_f[j0 + j]];
@@ -763,7 +782,35 @@ __device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &t
     // fewer than kRMax RHS the threads split into groups that take different A
     const int per = rt * Q, ngrp = blockDim.x / per;
     const int r = (threadIdx.x % per) / Q, t1 = threadIdx.x % Q;
-    if (threadIdx.x < ngrp * per) {
+    if (staged) {  // every thread is one (r, t1) row; all take every A of the chunk in turn
+      for (int ga = 0; ga < ga_n; ga++) {
+        float2 acc[Q];
+#pragma unroll
+        for (int t2 = 0; t2 < Q; t2++) acc[t2] = make_float2(0.f, 0.f);
+        for (int j = 0; j < ns; j++) {
+          const float2 v = cmul(pk[ga * maxsrc + j], fv[j * kRMax + r]);
+          const float w1 = w[j * 2 * Q + t1];
+          const float2 h = __fmul2_rn(make_float2(w1, w1), v);
+#pragma unroll
+          for (int t2 = 0; t2 < Q; t2++) acc[t2] = fma2s(w[j * 2 * Q + Q + t2], h, acc[t2]);
+        }
+        if (bulk && threadIdx.x == 0) bulk_wait_read0();  // the previous block's copy has read the stage
+        __syncthreads();
+#pragma unroll
+        for (int t2 = 0; t2 < Q; t2++) stage[r * Q2 + t1 * Q + t2] = cmul(post[ga * Q2 + t1 * Q + t2], acc[t2]);
+        if (bulk) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        float2 *dst = st + ((long long)(A0 + ga) * nB + box) * nrq + (long long)r0 * Q2;
+        if (bulk) {
+          if (threadIdx.x == 0) {
+            bulk_s2g(dst, stage, (uint32_t)(kRMax * Q2 * 8));
+            bulk_commit();
+          }
+        } else {
+          store_run(dst, stage, kRMax * Q2);
+        }
+      }
+    } else if (threadIdx.x < ngrp * per) {
       for (int ga = threadIdx.x / per; ga < ga_n; ga += ngrp) {
         float2 acc[Q];
 #pragma unroll
@@ -782,6 +829,7 @@ __device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &t
       }
     }
   }
+  if (bulk && threadIdx.x == 0) bulk_wait0();  // the bulk copies are done before the CTA ends
 }
 // Initialization CTA: one thread per (RHS, t1) row, kRMax q threads.
 template <int Q> struct InitShape {
@@ -791,8 +839,8 @@ constexpr int kInitChunk = 16;  // boxes A whose phases are staged together
 template <int Q>
 __global__ void __launch_bounds__(InitShape<Q>::threads) k32_init(Tables tb, TablesF tf, Phase ph, Geom g, int maxsrc,
                                                                    int GA, const float2 *__restrict__ f,
-                                                                   float2 *__restrict__ st) {
-  k32_init_body<Q>(tb, tf, ph, g, maxsrc, GA, f, st, blockIdx.x, blockIdx.y);
+                                                                   float2 *__restrict__ st, int use_stage) {
+  k32_init_body<Q>(tb, tf, ph, g, maxsrc, GA, f, st, blockIdx.x, blockIdx.y, use_stage != 0);
 }
 
 // FP32 conjugate transpose of the initialization (see k_init_adj).

@@ -278,8 +278,17 @@ template <typename R, int Q> struct Runner {
     if constexpr (sizeof(R) == 4) {
       if (fast32()) {
         int GA = std::min(kInitChunk, 1 << (2 * p.l0));
-        auto bytes = [&](int ga) { return (ms * kRMax + ga * ms + ga * Q2) * 8 + ms * 2 * Q * 4; };
+        // with 32 or more RHS: room for one staged output block (kRMax q^2 complex, 16-byte aligned)
+        int use_stage = nrhs >= kRMax ? 1 : 0;
+        auto bytes = [&](int ga) {
+          return (ms * kRMax + ga * ms + ga * Q2) * 8 + ms * 2 * Q * 4 + (use_stage ? 16 + kRMax * Q2 * 8 : 0);
+        };
         while (bytes(GA) > p.smem_optin && GA > 1) GA--;
+        if (bytes(GA) > p.smem_optin && use_stage) {
+          use_stage = 0;
+          GA = std::min(kInitChunk, 1 << (2 * p.l0));
+          while (bytes(GA) > p.smem_optin && GA > 1) GA--;
+        }
         if (bytes(GA) <= p.smem_optin) {
           const Geom g = geom(p.l0, kRMax, 1, p.nbox_init);
           dim3 grid((unsigned)p.nbox_init, (unsigned)((nrhs + kRMax - 1) / kRMax));
@@ -288,7 +297,7 @@ template <typename R, int Q> struct Runner {
           auto k = k32_init<Q>;
           set_smem(k, p.smem_optin);
           k<<<grid, InitShape<Q>::threads, bytes(GA), st>>>(p.tb, p.tf, p.ph, g, ms, GA, (const float2 *)f,
-                                                             (float2 *)out);
+                                                             (float2 *)out, use_stage);
           return check();
         }
       }

@@ -33,6 +33,8 @@
 // on expiry the kernel records status 1, stops issuing work, and still waits
 // (bounded) for its MMAs before freeing its tensor memory.
 #pragma once
+#include <type_traits>
+
 #include "fio_k32.cuh"
 
 namespace fio {
@@ -53,6 +55,21 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 }
 // D f32, A and B tf32, both K-major, N = 64, M = 128.
 constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Compile-time loop f(integral_constant<0>) .. f(integral_constant<N-1>), and a dispatch of
+// a runtime v in [0, N) to f(integral_constant<v>).
+template <int N, int I = 0, typename F> __device__ __forceinline__ void static_for(F &&f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<N, I + 1>(f);
+  }
+}
+template <int N, int I = 0, typename F> __device__ __forceinline__ void static_switch(int v, F &&f) {
+  if constexpr (I < N) {
+    if (v == I) f(std::integral_constant<int, I>{});
+    else static_switch<N, I + 1>(v, f);
+  }
+}
 
 // Round a finite FP32 value to TF32 (10 stored mantissa bits), to nearest with ties away
 // from zero: add half a TF32 unit to the magnitude bits and clear the 13 low bits (a
@@ -514,6 +531,13 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float *v) {
 #pragma unroll
   for (int c = 0; c < 8; c++) v[c] = __uint_as_float(r[c]);
 }
+// tcgen05.ld of 8 columns without the wait (the caller waits once for several loads).
+__device__ __forceinline__ void tc_ld8_issue(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
 __device__ __forceinline__ void tm_arrive(uint64_t *mbar) { mbar_arrive(mbar); }
 
 // handoff_ns: limit of the waits between the producer warps and the MMA warp (0: the
@@ -699,22 +723,28 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
       if (arows) {
         static_assert(RPW == 8, "epilogue reads 8 columns per warp");
         const uint32_t trow = tmem + C::ACC * d + RPW * wh + ((uint32_t)(32 * qd) << 16);
+        // every block's loads in flight at once, one wait; the wide accumulator's further
+        // 64-column blocks are then added in order
+        constexpr int NBK = W ? PB : 1;
+        uint32_t v[NBK][2][RPW];
+#pragma unroll
+        for (int blk = 0; blk < NBK; blk++)
+#pragma unroll
+          for (int h = 0; h < 2; h++) tc_ld8_issue(trow + 64 * blk + 32 * h, v[blk][h]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         float re[RPW], im[RPW];
-        tc_ld8(trow, re);
-        tc_ld8(trow + 32, im);
-        if (W) {  // the further 64-column blocks of the wide accumulator, added in order
 #pragma unroll
-          for (int blk = 1; blk < PB; blk++) {
-            float re2[RPW], im2[RPW];
-            tc_ld8(trow + 64 * blk, re2);
-            tc_ld8(trow + 64 * blk + 32, im2);
-#pragma unroll
-            for (int r = 0; r < RPW; r++) {
-              re[r] += re2[r];
-              im[r] += im2[r];
-            }
-          }
+        for (int r = 0; r < RPW; r++) {
+          re[r] = __uint_as_float(v[0][0][r]);
+          im[r] = __uint_as_float(v[0][1][r]);
         }
+#pragma unroll
+        for (int blk = 1; blk < NBK; blk++)
+#pragma unroll
+          for (int r = 0; r < RPW; r++) {
+            re[r] += __uint_as_float(v[blk][0][r]);
+            im[r] += __uint_as_float(v[blk][1][r]);
+          }
         if (o < Q2) {
           float2 *dst = out + pair_of(k) * nrq + (long long)(r0 + RPW * wh) * Q2 + o;
 #pragma unroll
@@ -756,57 +786,74 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
       // rho and s2), columns t walk G down a column
       const df rho_row = (!FWD && !sep) ? rhob[oc / Q] : df{0.f, 0.f};
       const df *grow = FWD ? gtb + oc * Q : gtb + oc % Q;
-      for (int c = 0; c < NCH; c++, gc++) {
+      // The chunks of a pair are unrolled at compile time (c) and each producer warp's
+      // columns are dispatched on its index among the quarter's warps (wh), so every column
+      // index is a constant: table reads take immediate offsets and the padding columns
+      // (i >= q^2) are zeros known at compile time.  Rows o >= q^2 (lanes of the M = 128
+      // padding) repeat row q^2 - 1: finite values in rows of D nobody reads.
+      static_for<NCH>([&](auto cI) {
+        constexpr int c = decltype(cI)::value;
+        if (!live) return;
         const int j = (int)(gc % C::NB);
-        if (gc >= C::NB && !pwait(&fre[j], (gc / C::NB - 1) & 1)) { live = false; break; }
+        if (gc >= C::NB && !pwait(&fre[j], (gc / C::NB - 1) & 1)) {
+          live = false;
+          return;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // A: this lane's row, CPW complex columns, both TF32 parts, into tensor memory.  The
-        // fast path is branch-free (indices clamped, invalid entries selected to zero) so the
-        // CPW independent phase chains interleave.
         if (arows) {
-          float p0[2 * CPW], p1[2 * CPW];
-          const int i0 = c * (C::KC / 2) + wh * CPW;  // first column of this warp
-#pragma unroll
-          for (int kk = 0; kk < CPW; kk++) {
-            const int i = i0 + kk;
-            const bool ok = ovalid && i < Q2;
-            const int ic = i < Q2 ? i : Q2 - 1;
-            float2 v;
-            if (!sep) {
-              df G, R;
-              if (FWD) {
-                const int s1 = ic / Q;
-                G = grow[ic - s1 * Q];
-                R = rhob[s1];
-              } else {
-                G = grow[ic * Q];
-                R = rho_row;
-              }
-              // theta = R G in double-float; (p - rint p) is exact, so the reduction mod 1
-              // needs no renormalisation of (p, lo)
-              const float p = R.h * G.h;
-              const float lo = __fmaf_rn(R.h, G.l, __fmaf_rn(R.l, G.h, __fmaf_rn(R.h, G.h, -p)));
-              const float r = (p - rintf(p)) + lo;
-              __sincosf(6.283185307179586f * r, &v.y, &v.x);
-            } else {
-              const int t = FWD ? oc : ic, s_ = FWD ? ic : oc;
-              v = expi<float>(theta_xp(ph, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q),
-                                       pn1(tb, lb, b1, s_ / Q, Q), pn2(tb, lb, b2, s_ % Q, Q)));
-            }
-            v.x = ok ? v.x : 0.f;
-            v.y = ok ? (FWD ? v.y : -v.y) : 0.f;
-            float pr_[kTcPA], pi_[kTcPA];
-            tf32_split<kTcPA>(v.x, pr_);
-            tf32_split<kTcPA>(v.y, pi_);
-            p0[2 * kk] = pr_[0];
-            p0[2 * kk + 1] = pi_[0];
-            p1[2 * kk] = pr_[1];
-            p1[2 * kk + 1] = pi_[1];
-          }
-          __syncwarp();
           const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + C::DC + j * C::AC + 2 * CPW * wh;
-          tm_st<2 * CPW>(ta, p0);
-          tm_st<2 * CPW>(ta + C::KC, p1);
+          if (!sep) {
+            static_switch<kTmPQ>(wh, [&](auto whI) {
+              constexpr int i0 = c * (C::KC / 2) + decltype(whI)::value * CPW;  // first column of this warp
+              float p0[2 * CPW], p1[2 * CPW];
+#pragma unroll
+              for (int kk = 0; kk < CPW; kk++) {
+                const int i = i0 + kk;
+                float2 v = make_float2(0.f, 0.f);
+                if (i < Q2) {
+                  // FWD: row o = x-node t, column i = (s1, s2); adjoint: row o = p-node s,
+                  // column i = x-node t (G read down the column of s2).  theta = R G in
+                  // double-float; (p - rint p) is exact, so the reduction mod 1 needs no
+                  // renormalisation of (p, lo)
+                  const df G = FWD ? grow[i % Q] : grow[i * Q];
+                  const df R = FWD ? rhob[i / Q] : rho_row;
+                  const float pp = R.h * G.h;
+                  const float lo = __fmaf_rn(R.h, G.l, __fmaf_rn(R.l, G.h, __fmaf_rn(R.h, G.h, -pp)));
+                  const float r = (pp - rintf(pp)) + lo;
+                  __sincosf(6.283185307179586f * r, &v.y, &v.x);
+                  if (!FWD) v.y = -v.y;
+                }
+                p0[2 * kk] = tf32_rna(v.x);
+                p0[2 * kk + 1] = tf32_rna(v.y);
+                p1[2 * kk] = tf32_rna(v.x - p0[2 * kk]);
+                p1[2 * kk + 1] = tf32_rna(v.y - p0[2 * kk + 1]);
+              }
+              __syncwarp();
+              tm_st<2 * CPW>(ta, p0);
+              tm_st<2 * CPW>(ta + C::KC, p1);
+            });
+          } else {  // separable phase: theta from the node coordinates, invalid entries zeroed
+            float p0[2 * CPW], p1[2 * CPW];
+            const int i0 = c * (C::KC / 2) + wh * CPW;
+#pragma unroll
+            for (int kk = 0; kk < CPW; kk++) {
+              const int i = i0 + kk;
+              const bool ok = ovalid && i < Q2;
+              const int ic = i < Q2 ? i : Q2 - 1;
+              const int t = FWD ? oc : ic, s_ = FWD ? ic : oc;
+              float2 v = expi<float>(theta_xp(ph, xn(tb, l, a1, t / Q, Q), xn(tb, l, a2, t % Q, Q),
+                                              pn1(tb, lb, b1, s_ / Q, Q), pn2(tb, lb, b2, s_ % Q, Q)));
+              v.x = ok ? v.x : 0.f;
+              v.y = ok ? (FWD ? v.y : -v.y) : 0.f;
+              p0[2 * kk] = tf32_rna(v.x);
+              p0[2 * kk + 1] = tf32_rna(v.y);
+              p1[2 * kk] = tf32_rna(v.x - p0[2 * kk]);
+              p1[2 * kk + 1] = tf32_rna(v.y - p0[2 * kk + 1]);
+            }
+            __syncwarp();
+            tm_st<2 * CPW>(ta, p0);
+            tm_st<2 * CPW>(ta + C::KC, p1);
+          }
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
         // B: lane r builds rows r and 32 + r of core-matrix column kc from X[r][s0], X[r][s0+1]
@@ -833,10 +880,12 @@ __global__ void __launch_bounds__(kTmThreads, 1) k32_switch_tm(Tables tb, Tables
             }
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // B went through the generic proxy: make it visible to the tensor core's async proxy
+        if (bidx >= 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         tm_arrive(&full[j]);
-      }
+        gc++;
+      });
       if (!live) break;
       if (k > 0 && !epilogue(k - 1)) break;
       if (su_of(k + 1) < nsu) {
