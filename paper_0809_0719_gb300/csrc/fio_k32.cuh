@@ -957,43 +957,50 @@ __device__ __forceinline__ void k32_term_body(const Tables &tb, const TablesF &t
         xd[idx] = xdesc(tf.ph, tf.xgrid[a1 * M + m / M], tf.xgrid[a2 * M + m % M]);
       }
     }
-  auto issue = [&](int B) {
-    if (B < nB) {
-      const float2 *src = st + ((long long)A * nB + B) * nrq + (long long)r0 * Q2;
-      float2 *dst = dbuf + (B & 1) * kRMax * Q2;
+  // Boxes B are walked angular index first (b2 outer, b1 inner): G(x, p0_2(B)) of the
+  // homogeneous phase theta = rho(p0_1) G(x, p0_2) is then evaluated once per b2 and kept
+  // in a register of the thread that owns the node (q^2 + M^2 <= 185 < blockDim nodes, one
+  // per thread); step k takes B = (k mod nb1) nb2 + k / nb1 and buffer k & 1.
+  const int nb1 = 1 << lb;
+  auto box_of = [&](int k) { return (k & (nb1 - 1)) * nb2 + (k >> lb); };
+  auto issue = [&](int k) {
+    if (k < nB) {
+      const float2 *src = st + ((long long)A * nB + box_of(k)) * nrq + (long long)r0 * Q2;
+      float2 *dst = dbuf + (k & 1) * kRMax * Q2;
       for (int idx = threadIdx.x; idx < rt * Q2; idx += blockDim.x) cp_async8(dst + idx, src + idx);
     }
     cp_async_commit();
   };
   issue(0);
   issue(1);
+  df gown = {0.f, 0.f};  // G(x_idx, p0_2) of the current b2, idx = threadIdx.x
   const int rr = threadIdx.x / M, m1o = threadIdx.x % M;  // accumulator owner (r, m1)
   const bool owner = threadIdx.x < rt * M;
   float ux[kTermM], uy[kTermM];
 #pragma unroll
   for (int m2 = 0; m2 < kTermM; m2++) ux[m2] = uy[m2] = 0.f;
   __syncthreads();
-  for (int B = 0; B < nB; B++) {
-    const int b1 = B / nb2, b2 = B % nb2;
-    float2 *pre = phb + (B & 1) * (Q2 + kTermM * kTermM);
+  for (int B_ = 0; B_ < nB; B_++) {  // step B_ of the walk
+    const int b1 = B_ & (nb1 - 1), b2 = B_ >> lb;
+    float2 *pre = phb + (B_ & 1) * (Q2 + kTermM * kTermM);
     float2 *post = pre + Q2;
-    const df rho = rhof(tb, tf, lb, b1, Q, Q);
-    const P2NodeF &c2f = p2f(tb, tf, lb, b2, Q, Q);
-    for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
+    const int idx = threadIdx.x;
+    if (idx < Q2 + M2) {
       float2 v;
       if (sep) {
         const XNode &x1 = idx < Q2 ? xn(tb, l, a1, idx / Q, Q) : tb.xgrid[a1 * M + (idx - Q2) / M];
         const XNode &x2 = idx < Q2 ? xn(tb, l, a2, idx % Q, Q) : tb.xgrid[a2 * M + (idx - Q2) % M];
         v = expi<float>(theta_xp(ph, x1, x2, pn1(tb, lb, b1, Q, Q), pn2(tb, lb, b2, Q, Q)));
       } else {
-        v = expi_df(df_mul(rho, g_eval(tf.ph, xd[idx], c2f)));
+        if (b1 == 0) gown = g_eval(tf.ph, xd[idx], p2f(tb, tf, lb, b2, Q, Q));
+        v = expi_df(df_mul(rhof(tb, tf, lb, b1, Q, Q), gown));
       }
       if (idx < Q2) pre[idx] = conjf2(v);
       else post[idx - Q2] = v;
     }
-    cp_async_wait(B + 1 < nB);
+    cp_async_wait(B_ + 1 < nB);
     __syncthreads();
-    const float2 *dv = dbuf + (B & 1) * kRMax * Q2;
+    const float2 *dv = dbuf + (B_ & 1) * kRMax * Q2;
     for (int task = threadIdx.x; task < rt * Q; task += blockDim.x) {
       const int t2 = task % Q, r = task / Q;
       float2 ym[kTermM];
@@ -1010,7 +1017,7 @@ __device__ __forceinline__ void k32_term_body(const Tables &tb, const TablesF &t
         if (m < M) y[(r * kTermM + m) * Q + t2] = ym[m];
     }
     __syncthreads();
-    issue(B + 2);
+    issue(B_ + 2);
     if (owner) {
       float2 yr[Q];
 #pragma unroll
@@ -1087,19 +1094,24 @@ __device__ __forceinline__ void k32_term_adj_body(const Tables &tb, const Tables
         xd[idx] = xdesc(tf.ph, tf.xgrid[a1 * M + m / M], tf.xgrid[a2 * M + m % M]);
       }
     }
-  for (int B = 0; B < nB; B++) {
-    const int b1 = B / nb2, b2 = B % nb2;
-    const df rho = rhof(tb, tf, lb, b1, Q, Q);
-    const P2NodeF &c2f = p2f(tb, tf, lb, b2, Q, Q);
+  // boxes B walked angular index first, G of the homogeneous phase evaluated once per b2
+  // by the thread that owns the node (as in k32_term_body)
+  const int nb1 = 1 << lb;
+  df gown = {0.f, 0.f};
+  for (int B_ = 0; B_ < nB; B_++) {
+    const int b1 = B_ & (nb1 - 1), b2 = B_ >> lb;
+    const int B = b1 * nb2 + b2;
     __syncthreads();  // gv/xd are ready; the previous B is done reading pre/post
-    for (int idx = threadIdx.x; idx < Q2 + M2; idx += blockDim.x) {
+    const int idx = threadIdx.x;
+    if (idx < Q2 + M2) {
       float2 v;
       if (sep) {
         const XNode &x1 = idx < Q2 ? xn(tb, l, a1, idx / Q, Q) : tb.xgrid[a1 * M + (idx - Q2) / M];
         const XNode &x2 = idx < Q2 ? xn(tb, l, a2, idx % Q, Q) : tb.xgrid[a2 * M + (idx - Q2) % M];
         v = expi<float>(theta_xp(ph, x1, x2, pn1(tb, lb, b1, Q, Q), pn2(tb, lb, b2, Q, Q)));
       } else {
-        v = expi_df(df_mul(rho, g_eval(tf.ph, xd[idx], c2f)));
+        if (b1 == 0) gown = g_eval(tf.ph, xd[idx], p2f(tb, tf, lb, b2, Q, Q));
+        v = expi_df(df_mul(rhof(tb, tf, lb, b1, Q, Q), gown));
       }
       if (idx < Q2) post[idx] = v;
       else pre[idx - Q2] = conjf2(v);
