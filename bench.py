@@ -694,14 +694,51 @@ def run_small(args):
     plan.close()
 
 
+def run_eq_sweep(args):
+    """--case eq: the cost of the accuracy knobs.  For the angular refinement e in {1, 2, 3} and
+    q in {7, 9, 11} (s = 3, ellipse [2, 1, 16, 1], N = --small-n): the FP32 apply time of 32 RHS
+    (CUDA events, the plan's autotuned kernels) and the relative l2 error of RHS 0 on 512 seeded x
+    against the FP64 direct sum of eq. dfio (fio_direct), for the FP32 form and the FP64 form."""
+    import torch
+
+    from paper_0809_0719_gb300 import fio
+    from paper_0809_0719_gb300.inputs import gaussian_batch, sample_indices
+
+    n, r = args.small_n, NRHS
+    F = gaussian_batch(n, range(r)).astype(np.complex64)
+    f = torch.from_numpy(F).cuda()
+    xi = torch.from_numpy(sample_indices(n, NSAMPLE, 1000)).cuda()
+    rows = []
+    ref = None
+    for e in (1, 2, 3):
+        for q in (7, 9, 11):
+            plan = fio.Plan(n, q, "ellipse", PARAMS, "f32", nrhs_max=r, s=S, e=e)
+            if ref is None:  # the direct sum does not depend on the plan's q and e
+                ref = plan.direct(f[:1], xi)[0].cpu().numpy()  # FP64 sums of the complex64 inputs
+            u = torch.empty_like(f)
+            ms = time_steps(lambda: plan.apply(f, out=u), args.steps, args.warmup, torch)
+            err32 = float(np.linalg.norm(u[0].reshape(-1)[xi].cpu().numpy() - ref) / np.linalg.norm(ref))
+            plan.close()
+            p64 = fio.Plan(n, q, "ellipse", PARAMS, "f64", nrhs_max=1, s=S, e=e)
+            u64 = p64.apply(f[:1].to(torch.complex128))
+            err64 = float(np.linalg.norm(u64[0].reshape(-1)[xi].cpu().numpy() - ref) / np.linalg.norm(ref))
+            p64.close()
+            rows.append({"e": e, "q": q, "ms_f32_32rhs": round(ms, 3), "rel_l2_err_f32": err32,
+                         "rel_l2_err_f64": err64})
+            torch.cuda.empty_cache()
+    print(json.dumps({"case": "eq", "N": n, "nrhs": r, "s": S, "phase": "ellipse [2,1,16,1]", "rows": rows}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default="full", choices=["full", "small", "batch"],
-                    help="small: N=256 q=9 16-RHS applies only (for profiler captures); batch: the uneven batch only")
+    ap.add_argument("--case", default="full", choices=["full", "small", "batch", "eq"],
+                    help="small: N=256 q=9 16-RHS applies only (for profiler captures); batch: the uneven batch "
+                         "only; eq: apply time and error over e in {1,2,3} x q in {7,9,11} at N=--small-n")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the uneven-batch measurement")
     ap.add_argument("--small-n", type=int, default=256, help="--case small: N")
     ap.add_argument("--small-nrhs", type=int, default=16, help="--case small: right-hand sides")
@@ -715,6 +752,9 @@ def main():
     args = ap.parse_args()
     if args.case == "small":
         run_small(args)
+        return
+    if args.case == "eq":
+        run_eq_sweep(args)
         return
     if args.case == "batch":
         import torch

@@ -136,7 +136,7 @@ long long kind_smem(int kind, int q, int s, int rs, const std::vector<BWork> &it
   case K_INIT:
     for (const BWork &w : its)
       b = std::max(b, ((long long)w.maxsrc * kRMax + (long long)w.GA * w.maxsrc + (long long)w.GA * Q2) * 8 +
-                          (long long)w.maxsrc * 2 * q * 4);
+                          (long long)w.maxsrc * 2 * q * 4 + (long long)w.GA * ((long long)sizeof(XDesc) + q * 8));
     return b;
   case K_INIT_ADJ:
     for (const BWork &w : its)

@@ -750,7 +750,9 @@ __device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &t
   float2 *pk = fv + maxsrc * kRMax;    // [GA][maxsrc]
   float2 *post = pk + GA * maxsrc;     // [GA][Q2]
   float *w = (float *)(post + GA * Q2);  // [maxsrc][2Q]
-  float2 *stage = (float2 *)(((uintptr_t)(w + maxsrc * 2 * Q) + 15) & ~(uintptr_t)15);  // [kRMax][Q2]
+  XDesc *xds = (XDesc *)(w + maxsrc * 2 * Q);  // [GA]: x-side data of the centre x0(A) of each A
+  df *gtab = (df *)(xds + GA);                 // [GA][Q]: G(x0(A), p2 node t2 of B)
+  float2 *stage = (float2 *)(((uintptr_t)(gtab + GA * Q) + 15) & ~(uintptr_t)15);  // [kRMax][Q2]
   const bool staged = use_stage && rt == kRMax && (int)blockDim.x == kRMax * Q;
   const bool bulk = staged && ((g.nrhs * Q2) & 1) == 0;
   for (int idx = threadIdx.x; idx < ns * rt; idx += blockDim.x) {
@@ -764,17 +766,42 @@ __device__ __forceinline__ void k32_init_body(const Tables &tb, const TablesF &t
   for (int A0 = 0; A0 < nA; A0 += GA) {
     const int ga_n = min(GA, nA - A0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < ga_n * (ns + Q2); idx += blockDim.x) {
-      const int ga = idx / (ns + Q2), k = idx % (ns + Q2);
-      const int A = A0 + ga, a1 = A >> l0, a2 = A & (nA1 - 1);
-      const XNode &x1 = xn(tb, l0, a1, Q, Q), &x2 = xn(tb, l0, a2, Q, Q);
-      const XNodeF &f1 = xnf(tb, tf, l0, a1, Q, Q), &f2 = xnf(tb, tf, l0, a2, Q, Q);
-      if (k < ns) {
-        pk[ga * maxsrc + k] = e32k(ph, tf, x1, x2, f1, f2, tb.src[j0 + k], tf.src[j0 + k]);
-      } else {
-        const int t = k - ns;
-        post[ga * Q2 + t] = conjf2(e32(ph, tf, x1, x2, f1, f2, pn1(tb, lb, b1, t / Q, Q), pn2(tb, lb, b2, t % Q, Q),
-                                       rhof(tb, tf, lb, b1, t / Q, Q), p2f(tb, tf, lb, b2, t % Q, Q)));
+    if (ph.id == 3) {  // separable phase: theta straight from the node coordinates
+      for (int idx = threadIdx.x; idx < ga_n * (ns + Q2); idx += blockDim.x) {
+        const int ga = idx / (ns + Q2), k = idx % (ns + Q2);
+        const int A = A0 + ga, a1 = A >> l0, a2 = A & (nA1 - 1);
+        const XNode &x1 = xn(tb, l0, a1, Q, Q), &x2 = xn(tb, l0, a2, Q, Q);
+        const XNodeF &f1 = xnf(tb, tf, l0, a1, Q, Q), &f2 = xnf(tb, tf, l0, a2, Q, Q);
+        if (k < ns) {
+          pk[ga * maxsrc + k] = e32k(ph, tf, x1, x2, f1, f2, tb.src[j0 + k], tf.src[j0 + k]);
+        } else {
+          const int t = k - ns;
+          post[ga * Q2 + t] = conjf2(e32(ph, tf, x1, x2, f1, f2, pn1(tb, lb, b1, t / Q, Q), pn2(tb, lb, b2, t % Q, Q),
+                                         rhof(tb, tf, lb, b1, t / Q, Q), p2f(tb, tf, lb, b2, t % Q, Q)));
+        }
+      }
+    } else {
+      // homogeneous phase: the x-side data of each x0(A) once, then the source phases
+      // theta(x0(A), k) and G(x0(A), p2_t2) (q per A), then the q^2 post factors
+      // e^{-2 pi i rho(p1_t1) G(x0(A), p2_t2)} as products
+      for (int ga = threadIdx.x; ga < ga_n; ga += blockDim.x) {
+        const int A = A0 + ga, a1 = A >> l0, a2 = A & (nA1 - 1);
+        xds[ga] = xdesc(tf.ph, xnf(tb, tf, l0, a1, Q, Q), xnf(tb, tf, l0, a2, Q, Q));
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < ga_n * (ns + Q); idx += blockDim.x) {
+        const int ga = idx / (ns + Q), k = idx % (ns + Q);
+        if (k < ns) {
+          const SrcF &kf = tf.src[j0 + k];
+          pk[ga * maxsrc + k] = expi_df(theta_k(tf.ph, xds[ga], kf.k1, kf.k2));
+        } else {
+          gtab[ga * Q + k - ns] = g_eval(tf.ph, xds[ga], p2f(tb, tf, lb, b2, k - ns, Q));
+        }
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < ga_n * Q2; idx += blockDim.x) {
+        const int ga = idx / Q2, t = idx % Q2;
+        post[ga * Q2 + t] = conjf2(expi_df(df_mul(rhof(tb, tf, lb, b1, t / Q, Q), gtab[ga * Q + t % Q])));
       }
     }
     __syncthreads();

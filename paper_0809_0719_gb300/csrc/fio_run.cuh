@@ -281,7 +281,8 @@ template <typename R, int Q> struct Runner {
         // with 32 or more RHS: room for one staged output block (kRMax q^2 complex, 16-byte aligned)
         int use_stage = nrhs >= kRMax ? 1 : 0;
         auto bytes = [&](int ga) {
-          return (ms * kRMax + ga * ms + ga * Q2) * 8 + ms * 2 * Q * 4 + (use_stage ? 16 + kRMax * Q2 * 8 : 0);
+          return (ms * kRMax + ga * ms + ga * Q2) * 8 + ms * 2 * Q * 4 + ga * ((int)sizeof(XDesc) + Q * 8) +
+                 (use_stage ? 16 + kRMax * Q2 * 8 : 0);
         };
         while (bytes(GA) > p.smem_optin && GA > 1) GA--;
         if (bytes(GA) > p.smem_optin && use_stage) {
