@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(4 * kRT, 2)
     k32_trans_rp(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm, const float2 *__restrict__ in,
                  float2 *__restrict__ out, int *status) {
   constexpr int Q2 = Q * Q;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // bulk copies need 16-byte alignment
   uint64_t *mbar = (uint64_t *)smem_raw;                  // [2]: inputs of i1 = 0 and i1 = 1
   float2 *ph_s = (float2 *)(smem_raw + 16);               // pre [4 j][4 i][Q2] | post [4 j][Q2]
   float2 *in_s = ph_s + 20 * Q2;                          // [4 i][kRT][Q2]; output staging [4 j][kRT][Q2]
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(4 * kRT, 2)
     k32_trans_rx(Tables tb, TablesF tf, Phase ph, Geom g, TMat<float, Q> tm, const float2 *__restrict__ in,
                  float2 *__restrict__ out, int *status) {
   constexpr int Q2 = Q * Q;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // bulk copies need 16-byte alignment
   uint64_t *mbar = (uint64_t *)smem_raw;                 // [2]: ring slots
   float2 *ph_s = (float2 *)(smem_raw + 16);              // pre [4 i][Q2] | post [4 j][4 i][Q2]
   float2 *ring = ph_s + 20 * Q2;                         // [2 slot][kRT][Q2]
