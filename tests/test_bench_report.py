@@ -18,7 +18,7 @@ PROF = {"init": (2, 89.1), "trans_p": (4, 306.7), "switch": (2, 316.8), "trans_x
 MS_STEP = 567.9
 
 
-@pytest.mark.parametrize("switch_impl", [0, 3])
+@pytest.mark.parametrize("switch_impl", [0, 3, 5, 6])
 def test_kernel_report(switch_impl):
     kernels, roof = bench.kernel_report(PROF, INFO, 2, switch_impl)
     assert sum(v["share"] for v in kernels.values()) == pytest.approx(1.0, abs=2e-3)
@@ -36,13 +36,14 @@ def test_kernel_report(switch_impl):
     # state, 26 ms at the HBM peak, bound it) but 87 ms on the FP32 FMA pipe
     sw = kernels["switch"]
     swfl = 8 * 9 ** 4 * INFO.pairs_per_level * 32
-    if switch_impl == 3:
+    tensor = switch_impl in (3, 5, 6)  # the tcgen05 forms (5 or 3 split-TF32 products, narrow or wide)
+    if tensor:
         assert sw["bound"] == "hbm"
         assert sw["frac"] == pytest.approx(by / (bench._hbm_peak_gbs() * 1e9) / 158.4e-3, abs=1e-3)
     else:
         assert sw["bound"] == "alu"
         assert sw["frac"] == pytest.approx(swfl / bench.FP32_PEAK / 158.4e-3, abs=1e-3)
-    assert sw["pipe"] == ("tf32 tensor" if switch_impl == 3 else "fp32 fma")
+    assert sw["pipe"] == ("tf32 tensor" if tensor else "fp32 fma")
     # init and term move 87 GB (13 ms) against 0.7-0.8e12 flops (9-10 ms): HBM-bound too
     assert kernels["init"]["bound"] == "hbm" and kernels["term"]["bound"] == "hbm"
 
